@@ -1,0 +1,415 @@
+"""Benchmark of the fixed-radius nearest-neighbour graph build on B300.
+
+Workload (the graph-building step of the paper's pipeline, Sec. 3.4 / Table 1,
+on synthetic TrackML-shaped embeddings): events of N=120,000 points, D=8
+float32 coordinates on the 1/256 grid, r=0.1, K=256.  A step builds the graphs
+of a batch of 64 such events (each with its own seed) in one batched build
+replayed from a captured CUDA graph.  Beside it:
+
+* plain: the same events built one per call (one graph replay per event),
+  with per-event device latency p50/p99;
+* e2e: the batched build through the host-to-host C call
+  (frnn_build_graph_host): points copied from pinned host memory, the whole
+  CSR copied back, all inside the timed region;
+* roofline: per-stage device times from CUDA events between the stages
+  (frnn_build_graph_profiled) for the dominant kernel, against the measured
+  HBM bandwidth;
+* cpu_baseline: the CPU oracle (brute force, OpenMP) on a bounded sample of
+  queries of one event, scaled to events/s.
+
+`--impl reference` times the CPU oracle alone as the reference arm.
+Multi-GPU (torchrun): every rank builds its own events (replicas, no
+collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2202_06929_b300 import synth  # noqa: E402
+
+METRIC = "FRNN graph-build events/s at N=120k,D=8 batched vs plain; p50/p99 latency"
+UNIT = "events/s"
+N_PER_EVENT, D, R, K = 120_000, 8, 0.1, 256
+KERNELS_PER_BUILD = 7
+STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_count", "scan_rows", "walk_fill")
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--events", type=int, default=64, help="events per batched step")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-queries", type=int, default=40_000,
+                    help="queries of the CPU oracle sample (bounded CPU work)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- workload
+
+def make_batch(rank: int, n_events: int):
+    """Events rank*n_events .. of the N=120k workload, concatenated."""
+    evs = [synth.make_event("c2", rank * n_events + e) for e in range(n_events)]
+    off = np.zeros(n_events + 1, dtype=np.int64)
+    off[1:] = np.cumsum([e.shape[0] for e in evs])
+    return np.ascontiguousarray(np.concatenate(evs)), off
+
+
+def percentile(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self._t:
+                self._t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- peaks
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def stage_bytes(n_total: int, n_edges: int, d: int):
+    """Algorithmic bytes of each stage for a batch (each stage's unavoidable
+    reads of its inputs and writes of its outputs, counted once)."""
+    dp = (d + 3) // 4 * 4
+    return {
+        "bbox_plan": 4 * n_total * d,
+        "key_hist": 4 * n_total * d + 8 * n_total,
+        "scan_cells": 0,  # size of the cell table, reported separately
+        "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total,
+        "walk_count": 4 * n_total * dp + 8 * n_total,
+        "scan_rows": 8 * n_total,
+        "walk_fill": 4 * n_total * dp + 4 * (n_total + 1) + 4 * n_edges + 4 * n_total,
+    }
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def run_cpu_baseline(x, queries: int, seed: int = 0):
+    import oracle
+    n = x.shape[0]
+    q = np.random.default_rng(seed).choice(n, size=min(queries, n), replace=False)
+    t0 = time.perf_counter()
+    oracle.radius_graph(x, R, K, queries=q)
+    dt = time.perf_counter() - t0
+    return {"value": (len(q) / n) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(q)} random query rows of one N={n} event (brute force over all {n} points), "
+                      f"{dt:.2f} s; events/s = (rows / N) / s"}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    x = synth.make_event("c2", 0)
+    steps, warm = [], []
+    for i in range(args.warmup):
+        warm.append(run_cpu_baseline(x, max(args.cpu_queries // 20, 100), seed=1000 + i))
+    per_step_q = max(args.cpu_queries // max(args.steps, 1), 200)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        steps.append(run_cpu_baseline(x, per_step_q, seed=i))
+    wall = time.perf_counter() - t0
+    value = (args.steps * per_step_q / x.shape[0]) / wall
+    cores = steps[0]["cores"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "c2: N=120000, D=8, r=0.1, K=256 (CPU oracle on a query sample per step)",
+                   "n_per_event": N_PER_EVENT, "d": D, "r": R, "k": K},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step_q} random query rows of one N={N_PER_EVENT} event per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        rc = reference_arm(args, rank, world)
+        if pg is not None:
+            pg.destroy_process_group()
+        return rc
+
+    import torch
+    import paper_2202_06929_b300 as frnn
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B = args.events
+    x_host, off = make_batch(rank, B)
+    n_total = int(off[-1])
+    x_dev = torch.from_numpy(x_host).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    plan = frnn.Plan(n_max=n_total, d_max=D, k_max_cap=K, events_max=B, edge_capacity=n_total * 64,
+                     use_graph=True, device=local)
+    plan_one = frnn.Plan(n_max=N_PER_EVENT, d_max=D, k_max_cap=K, events_max=1,
+                         edge_capacity=N_PER_EVENT * 64, use_graph=True, device=local)
+
+    # ---- batched: the timed step
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.build_batched(x_dev, off, R, K, stream=stream)
+        st = plan.last_status(stream)
+        if st != 0:
+            raise RuntimeError(f"warm-up status: {frnn.status_string(st)}")
+        n_edges = int(plan.build_batched(x_dev, off, R, K, stream=stream).n_edges())
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            ev[0].record(stream)
+            for i in range(args.steps):
+                plan.build_batched(x_dev, off, R, K, stream=stream)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize(dev)
+        barrier(pg)
+    st = plan.last_status(stream)
+    if st != 0:
+        raise RuntimeError(f"timed-region status: {frnn.status_string(st)}")
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms_max = max_over_ranks(pg, total_ms, dev)
+    events_all = sum_over_ranks(pg, float(B * args.steps), dev)
+    value = events_all / (total_ms_max / 1e3)
+
+    # ---- plain: one event per call, cycling through the batch's events (the
+    # batch is 2x larger than L2, so each event's input is cold when reused)
+    plain_ms = []
+    with torch.cuda.stream(stream):
+        for e in range(min(B, 4)):
+            lo, hi = int(off[e]), int(off[e + 1])
+            plan_one.build(x_dev[lo:hi], R, K, stream=stream)
+        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * B)]
+        torch.cuda.synchronize(dev)
+        for e in range(B):
+            lo, hi = int(off[e]), int(off[e + 1])
+            pe[2 * e].record(stream)
+            plan_one.build(x_dev[lo:hi], R, K, stream=stream)
+            pe[2 * e + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = [pe[2 * e].elapsed_time(pe[2 * e + 1]) for e in range(B)]
+        plain_wall = pe[0].elapsed_time(pe[-1])
+    st = plan_one.last_status(stream)
+    if st != 0:
+        raise RuntimeError(f"plain status: {frnn.status_string(st)}")
+    plain_value = B / (plain_wall / 1e3)
+
+    # ---- per-stage times of the batched build (CUDA events between stages)
+    stage_ms = {s: [] for s in STAGES}
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            _, ms = plan.build_profiled(x_dev, off, R, K, stream=stream)
+            for s in STAGES:
+                stage_ms[s].append(ms[s])
+    stage_avg = {s: float(np.mean(v[1:])) for s, v in stage_ms.items()}
+    dom = max(stage_avg, key=stage_avg.get)
+    sbytes = stage_bytes(n_total, n_edges, D)
+    hbm_peak, peak_kind = measured_peaks()
+    achieved = sbytes[dom] / (stage_avg[dom] / 1e3) / 1e9
+    whole_bytes = 4 * n_total * D + 4 * (n_total + 1) + 4 * n_edges
+
+    # ---- e2e: host buffers in, host CSR out, through the C call
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+        pinned_x = torch.from_numpy(x_host).pin_memory()
+        out = dict(row_ptr=torch.zeros(n_total + 1, dtype=torch.int32).pin_memory().numpy(),
+                   col=torch.zeros(n_total * 64, dtype=torch.int32).pin_memory().numpy(),
+                   edge_off=np.zeros(B + 1, np.int32))
+        xin = pinned_x.numpy()
+        plan.build_host(xin, off, R, K, out=out, stream=stream)
+        torch.cuda.synchronize(dev)
+        e2e_steps = max(3, min(args.steps, 10))
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.build_host(xin, off, R, K, out=out, stream=stream)
+        t1 = time.perf_counter()
+        barrier(pg)
+        e2e_s = max_over_ranks(pg, t1 - t0, dev)
+        e2e = {"value": sum_over_ranks(pg, float(B * e2e_steps), dev) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(x_host.nbytes),
+               "d2h_bytes_per_step": int(4 * (n_total + 1) + 4 * out["n_edges"] + 4 * (B + 1)),
+               "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+               "note": "frnn_build_graph_host: H2D of the points from pinned memory, build, D2H of "
+                       "row_ptr, edge_off and col, host wall clock"}
+        del ctypes
+
+    # ---- CPU oracle baseline (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(x_host[off[0]:off[1]], args.cpu_queries)
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"c2 batched: {B} events x N=120000 (seeded per event), D=8, r=0.1, K=256, "
+                            "one batched build per step replayed from a CUDA graph",
+                "events_per_step": B, "n_per_event": N_PER_EVENT, "d": D, "r": R, "k": K,
+                "points_per_step": n_total, "edges_per_step": n_edges,
+                "l2": f"inputs larger than L2 ({x_host.nbytes / 1e6:.0f} MB of points per step, "
+                      f"plus {4 * n_edges / 1e6:.0f} MB of col written)",
+                "parallelism": f"replicas x{world}",
+            },
+            "batched": {"events_per_s": value, "step_ms_p50": percentile(step_ms, 50),
+                        "step_ms_p99": percentile(step_ms, 99),
+                        "event_latency_note": "every event of a batch completes with its step"},
+            "plain": {"events_per_s": plain_value, "latency_ms_p50": percentile(plain_ms, 50),
+                      "latency_ms_p99": percentile(plain_ms, 99),
+                      "note": "one event per call (CUDA graph replay per event), device time per event"},
+            "batched_over_plain": value / plain_value / world,
+            "stages_ms": stage_avg,
+            "roofline": {"bound": "hbm", "kernel": f"k_walk_{dom.split('_')[-1]}" if dom.startswith("walk") else dom,
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": sbytes[dom],
+                         "launch_ms": stage_avg[dom],
+                         "whole_build": {"algorithmic_bytes": whole_bytes,
+                                         "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
+                                         "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak}},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": KERNELS_PER_BUILD * args.steps,
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                       "reasons": clocks["reasons"]},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    plan_one.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

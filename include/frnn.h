@@ -1,0 +1,196 @@
+/*
+ * frnn.h - C ABI of libfrnn, a fixed-radius nearest-neighbour (FRNN) graph
+ * builder for NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper: "Accelerating the Inference of the Exa.TrkX Pipeline",
+ * Sec. 2 and Sec. 3.4): given n points embedded in a d-dimensional space and a
+ * radius r, join every point i to the other points j whose Euclidean distance
+ * is within r.  Each row keeps at most k_max neighbours, the nearest ones
+ * (Sec. 3.1: exact k-nearest-neighbour search followed by a radius cut).
+ * Precisely, with d2(i,j) the float32 sum over t = 0..d-1, in that order, of
+ * (x[i][t] - x[j][t])^2 (each subtraction, product and addition rounded once)
+ * and r2 = fl32(r * r):
+ *
+ *     S_i   = { j != i : d2(i,j) <= r2 }
+ *     row i = the min(|S_i|, k_max) members of S_i that are smallest by the
+ *             pair (d2(i,j), j), listed in increasing (d2, j) order.
+ *
+ * The result is a CSR graph with directed edges i -> j.  It is bit-exact and
+ * deterministic: it does not depend on the device, the launch shape or the
+ * batch an event is built in.
+ *
+ * Conventions for every function:
+ *   - Pointers documented as "device" must be device memory of the plan's
+ *     device; "host" pointers are ordinary (or pinned) host memory.
+ *   - Streams are passed as void* (a cudaStream_t; NULL = the legacy default
+ *     stream).  Build calls are asynchronous on that stream unless stated.
+ *   - Every function returns an frnn_status; no C++ exception crosses the ABI.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *     Errors found by kernels (non-finite input, an exhausted edge buffer, a
+ *     bounded wait that ran out) are latched in a device status word and
+ *     reported by frnn_get_last_status().
+ *   - A plan is not thread-safe: use one plan per host thread or per stream.
+ */
+#ifndef FRNN_H
+#define FRNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FRNN_API __attribute__((visibility("default")))
+#else
+#define FRNN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FRNN_OK = 0,
+    FRNN_ERR_INVALID_ARG = 1,     /* bad pointer, size, radius or cap; see each call   */
+    FRNN_ERR_CUDA = 2,            /* a CUDA runtime call failed                         */
+    FRNN_ERR_OOM = 3,             /* device allocation failed                           */
+    FRNN_ERR_NONFINITE_INPUT = 4, /* an event holds NaN or Inf; its rows are left empty */
+    FRNN_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                 */
+    FRNN_ERR_OVERFLOW = 6,        /* the edges did not fit the plan's edge capacity     */
+    FRNN_ERR_CAPACITY = 7         /* the call exceeds a capacity fixed at plan creation */
+} frnn_status;
+
+/* Plan flags. */
+#define FRNN_EMIT_D2 0x1u    /* also write the float32 d2 of every edge              */
+#define FRNN_USE_GRAPH 0x2u  /* replay the build as a CUDA graph captured on first use */
+
+typedef struct frnn_plan frnn_plan; /* opaque; owns all device scratch and outputs */
+
+typedef struct {
+    int device;            /* CUDA device ordinal                                     */
+    int d_max;             /* largest embedding dimension a call may use, 1..64       */
+    int64_t n_max;         /* largest total point count of one call (sum over events) */
+    int events_max;        /* largest number of events in one call, >= 1             */
+    int k_max_cap;         /* largest neighbour cap of one call, 1..1024              */
+    int64_t edge_capacity; /* col slots; 0 = n_max * k_max_cap (never overflows)      */
+    int cells_per_point;   /* cell-table slots per point (plus 4096 per event); 0 = 4 */
+    uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH                           */
+} frnn_plan_params;
+
+/*
+ * Output of a build: one CSR over all events of the call, in event order.
+ * Event b owns points ev_off[b] .. ev_off[b+1]-1 of the call (ev_off from the
+ * call) and edges edge_off[b] .. edge_off[b+1]-1.  For point p of the call,
+ * its row is col[row_ptr[p] .. row_ptr[p+1]-1]; col holds point indices LOCAL
+ * to the event (0 .. n_b - 1).  Every pointer is device memory owned by the
+ * plan and stays valid until the next build on the plan or its destruction.
+ */
+typedef struct {
+    const int32_t* row_ptr;  /* device, n_total + 1 entries, row_ptr[0] = 0           */
+    const int32_t* col;      /* device, n_edges entries used                           */
+    const float* d2;         /* device, n_edges entries, or NULL without FRNN_EMIT_D2  */
+    const int32_t* edge_off; /* device, n_events + 1 entries                           */
+    const int32_t* n_edges;  /* device scalar: total edges (= edge_off[n_events])      */
+    int n_events;
+    int64_t n_total;
+} frnn_csr;
+
+/*
+ * Cell-grid tuning (speed only; the result never depends on it).
+ * g_max: most hashed dimensions, 1..4 (0 = 4).  cell_scale: cell edge / r,
+ * >= 1 (0 = 1).  The dimensions hashed are always the ones of widest extent.
+ */
+typedef struct {
+    int g_max;
+    float cell_scale;
+} frnn_tuning;
+
+/*
+ * Create a plan: allocates every device buffer a call within the given
+ * capacities needs, so builds never allocate.  *out receives the plan.
+ * Errors: INVALID_ARG (out or p NULL, a capacity out of range, or
+ * n_max * k_max_cap >= 2^31 with edge_capacity = 0), CUDA, OOM.
+ */
+FRNN_API int frnn_plan_create(frnn_plan** out, const frnn_plan_params* p);
+
+/* Free every buffer of the plan (synchronises its device).  NULL is a no-op. */
+FRNN_API int frnn_plan_destroy(frnn_plan* plan);
+
+/* Set / read the cell-grid tuning used by the following builds. */
+FRNN_API int frnn_plan_set_tuning(frnn_plan* plan, const frnn_tuning* t);
+FRNN_API int frnn_plan_get_tuning(const frnn_plan* plan, frnn_tuning* t);
+
+/*
+ * Build the graph of one event (Sec. 2, Sec. 3.4; the cap of Sec. 3.1).
+ *   emb    device, float32, row-major [n][d] with row stride d, caller-owned;
+ *          it must stay unchanged until the stream reaches the end of the build.
+ *   n      points, 0 <= n <= n_max.       d  dimension, 1 <= d <= d_max.
+ *   r      radius, finite and > 0.        k_max  cap, 1 <= k_max <= k_max_cap.
+ *   stream cudaStream_t the work is enqueued on (asynchronous; no host sync).
+ *   out    receives the plan-owned device pointers (n_events = 1).
+ * Errors: INVALID_ARG (NULL plan/out, NULL emb with n > 0, sizes out of range,
+ * n * k_max >= 2^31), CAPACITY (n > n_max, d > d_max, k_max > k_max_cap), CUDA.
+ */
+FRNN_API int frnn_build_graph(frnn_plan* plan, const float* emb, int64_t n, int d, float r, int k_max,
+                     void* stream, frnn_csr* out);
+
+/*
+ * Build the graphs of several independent events in one pass of the kernels.
+ *   emb      device, float32 [ev_off[n_events]][d]: the events' points concatenated.
+ *   ev_off   HOST array of n_events + 1 offsets, ev_off[0] = 0, non-decreasing
+ *            (empty events are allowed).  Read before the call returns.
+ *   n_events 1 <= n_events <= events_max.  Other arguments as frnn_build_graph.
+ * Each event's rows are identical to those a separate frnn_build_graph call
+ * would give.  Errors: as frnn_build_graph, plus INVALID_ARG for bad offsets.
+ */
+FRNN_API int frnn_build_graph_batched(frnn_plan* plan, const float* emb, const int64_t* ev_off, int n_events,
+                             int d, float r, int k_max, void* stream, frnn_csr* out);
+
+/*
+ * Host-to-host form (the whole call a CPU-side user makes): copies the
+ * events' points from host memory to the device, builds, and copies the CSR
+ * back.  Synchronous: returns when the host buffers are filled.
+ *   h_emb       host float32 [ev_off[n_events]][d] (pinned memory is faster).
+ *   h_row_ptr   host int32 [ev_off[n_events] + 1], receives row_ptr.
+ *   h_col       host int32 [col_capacity], receives col.
+ *   h_edge_off  host int32 [n_events + 1] or NULL.
+ *   h_n_edges   host int64, receives the edge count (also when it exceeds
+ *               col_capacity, in which case the call returns OVERFLOW and
+ *               h_col is not written).
+ * Errors: as frnn_build_graph_batched, plus OVERFLOW, and any status the
+ * device latched during this build.
+ */
+FRNN_API int frnn_build_graph_host(frnn_plan* plan, const float* h_emb, const int64_t* ev_off,
+                          int n_events, int d, float r, int k_max, int32_t* h_row_ptr,
+                          int32_t* h_col, int64_t col_capacity, int32_t* h_edge_off,
+                          int64_t* h_n_edges, void* stream);
+
+/*
+ * frnn_build_graph_batched with a CUDA event recorded between the stages,
+ * for profiling.  Never replays a CUDA graph.  Synchronous: waits for the
+ * build, then writes the device time of each stage in milliseconds to
+ * stage_ms[0..6]: bounding box and cell grid, cell ids and histogram, cell
+ * scan, scatter into cell order, count walk, row scan, fill walk.
+ * n_stages must be >= 7.  Errors: as frnn_build_graph_batched.
+ */
+FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const int64_t* ev_off,
+                                       int n_events, int d, float r, int k_max, void* stream,
+                                       frnn_csr* out, float* stage_ms, int n_stages);
+
+/*
+ * Synchronise `stream`, then return and clear the status latched by the
+ * plan's kernels since the last call (FRNN_OK if none).  If several errors
+ * were latched the most severe is returned, in the order TIMEOUT, OVERFLOW,
+ * NONFINITE_INPUT.  A CUDA error on the stream returns FRNN_ERR_CUDA.
+ */
+FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
+
+/* Static English description of a status code (never NULL). */
+FRNN_API const char* frnn_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+FRNN_API int frnn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRNN_H */

@@ -1,0 +1,528 @@
+// Host side of libfrnn: plans, the C ABI declared in include/frnn.h, and the
+// CUDA-graph replay of a build.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "frnn.h"
+#include "frnn_internal.h"
+
+using namespace frnn;
+
+namespace {
+
+constexpr int kRing = 4;  // pinned staging slots for the per-call header
+constexpr int kVersion = 10000;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct GraphEntry {
+    int dp4 = 0;
+    int cap = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct frnn_plan {
+    frnn_plan_params prm{};
+    frnn_tuning tuning{4, 1.0f};
+    int n_sm = 0;
+    int dp_max = 0;
+    long long cells_max = 0;
+    long long edge_cap = 0;
+    int tiles_cells = 0, tiles_rows = 0;
+    LaunchCfg base_cfg{};
+    DevState st{};
+    // per-call header + event table (device) and its pinned staging ring
+    char* d_call = nullptr;
+    size_t call_bytes = 0;
+    char* h_call[kRing] = {};
+    cudaEvent_t ring_ev[kRing] = {};
+    int ring_pos = 0;
+    // allocations to free
+    void* allocs[40] = {};
+    int n_allocs = 0;
+    // graph cache (FRNN_USE_GRAPH)
+    cudaStream_t cap_stream = nullptr;
+    GraphEntry graphs[32];
+    int n_graphs = 0;
+    // walk launch shapes per (dp4, cap)
+    LaunchCfg walk_cfg[17][12];
+    bool walk_ok[17][12] = {};
+    // device input of the host-to-host call
+    float* d_input = nullptr;
+    long long d_input_floats = 0;
+    frnn_csr last{};
+};
+
+namespace {
+
+template <typename T>
+int plan_alloc(frnn_plan* p, T** out, long long count)
+{
+    *out = nullptr;
+    if (count <= 0) count = 1;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, (size_t)count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_OOM;
+    }
+    p->allocs[p->n_allocs++] = ptr;
+    *out = static_cast<T*>(ptr);
+    return FRNN_OK;
+}
+
+void plan_free_all(frnn_plan* p)
+{
+    for (int i = 0; i < p->n_graphs; ++i)
+        if (p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
+    p->n_graphs = 0;
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (int i = 0; i < kRing; ++i) {
+        if (p->ring_ev[i]) cudaEventDestroy(p->ring_ev[i]);
+        if (p->h_call[i]) cudaFreeHost(p->h_call[i]);
+    }
+    for (int i = 0; i < p->n_allocs; ++i) cudaFree(p->allocs[i]);
+    p->n_allocs = 0;
+    if (p->d_input) cudaFree(p->d_input);
+}
+
+// Restore every buffer that must be zero (or +-inf encoded) between builds.
+int reset_device_state(frnn_plan* p, cudaStream_t s)
+{
+    const DevState& st = p->st;
+    const long long ev = p->prm.events_max;
+    bool ok = true;
+    ok &= cudaMemsetAsync(st.bb_min, 0xff, sizeof(unsigned) * ev * kMaxDims, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.bb_max, 0, sizeof(unsigned) * ev * kMaxDims, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.chunk_done, 0, sizeof(unsigned) * ev, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.nonfinite, 0, sizeof(unsigned) * ev, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.counters, 0, sizeof(unsigned) * kCtrCount, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.cell_count, 0, sizeof(unsigned) * p->cells_max, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.scan_cells, 0, sizeof(unsigned long long) * p->tiles_cells, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.scan_rows, 0, sizeof(unsigned long long) * p->tiles_rows, s) == cudaSuccess;
+    return ok ? FRNN_OK : FRNN_ERR_CUDA;
+}
+
+int get_walk_cfg(frnn_plan* p, int dp4, int cap, LaunchCfg* out)
+{
+    int ci = 0;
+    while ((1 << ci) < cap) ++ci;
+    if (dp4 < 1 || dp4 > 16 || ci >= 12) return FRNN_ERR_INVALID_ARG;
+    if (!p->walk_ok[dp4][ci]) {
+        LaunchCfg c = p->base_cfg;
+        if (config_walk(dp4, cap, p->n_sm, &c) != 0) {
+            cudaGetLastError();
+            return FRNN_ERR_CUDA;
+        }
+        p->walk_cfg[dp4][ci] = c;
+        p->walk_ok[dp4][ci] = true;
+    }
+    *out = p->walk_cfg[dp4][ci];
+    return FRNN_OK;
+}
+
+int launch(frnn_plan* p, int dp4, int cap, cudaStream_t s, cudaEvent_t* stage_ev)
+{
+    LaunchCfg cfg;
+    int rc = get_walk_cfg(p, dp4, cap, &cfg);
+    if (rc != FRNN_OK) return rc;
+    if (stage_ev || !(p->prm.flags & FRNN_USE_GRAPH))
+        return launch_build(p->st, dp4, cfg, s, stage_ev) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
+    GraphEntry* ge = nullptr;
+    for (int i = 0; i < p->n_graphs; ++i)
+        if (p->graphs[i].dp4 == dp4 && p->graphs[i].cap == cap) ge = &p->graphs[i];
+    if (!ge) {
+        if (p->n_graphs >= 32) return FRNN_ERR_CAPACITY;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return FRNN_ERR_CUDA;
+        const int lrc = launch_build(p->st, dp4, cfg, p->cap_stream, nullptr);
+        const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+        if (lrc != 0 || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return FRNN_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            return FRNN_ERR_CUDA;
+        }
+        ge = &p->graphs[p->n_graphs++];
+        ge->dp4 = dp4;
+        ge->cap = cap;
+        ge->exec = ex;
+    }
+    return cudaGraphLaunch(ge->exec, s) == cudaSuccess ? FRNN_OK : FRNN_ERR_CUDA;
+}
+
+int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
+                     int d, float r, int k, frnn_csr* out, long long* n_total)
+{
+    if (!p || !out || !ev_off) return FRNN_ERR_INVALID_ARG;
+    if (n_events < 1 || d < 1 || d > kMaxDims || k < 1 || k > 1024) return FRNN_ERR_INVALID_ARG;
+    if (!(r > 0.0f) || !std::isfinite(r)) return FRNN_ERR_INVALID_ARG;
+    if (ev_off[0] != 0) return FRNN_ERR_INVALID_ARG;
+    for (int b = 0; b < n_events; ++b)
+        if (ev_off[b + 1] < ev_off[b]) return FRNN_ERR_INVALID_ARG;
+    const long long n = ev_off[n_events];
+    if (n > 0 && (!emb || (reinterpret_cast<uintptr_t>(emb) & 3u))) return FRNN_ERR_INVALID_ARG;
+    if (n * (long long)k >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+    if (n_events > p->prm.events_max || n > p->prm.n_max || d > p->prm.d_max || k > p->prm.k_max_cap)
+        return FRNN_ERR_CAPACITY;
+    float r2 = r * r;
+    if (!(r2 > 0.0f) || !std::isfinite(r2)) return FRNN_ERR_INVALID_ARG;
+    *n_total = n;
+    return FRNN_OK;
+}
+
+int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d,
+                  float r, int k, cudaStream_t s, frnn_csr* out, cudaEvent_t* stage_ev = nullptr)
+{
+    long long n_total = 0;
+    int rc = check_build_args(p, emb, ev_off, n_events, d, r, k, out, &n_total);
+    if (rc != FRNN_OK) return rc;
+    const DevState& st = p->st;
+    out->row_ptr = st.row_ptr;
+    out->col = st.col;
+    out->d2 = (p->prm.flags & FRNN_EMIT_D2) ? st.d2 : nullptr;
+    out->edge_off = st.edge_off;
+    out->n_edges = st.edge_off + n_events;
+    out->n_events = n_events;
+    out->n_total = n_total;
+    if (n_total == 0) {
+        if (cudaMemsetAsync(st.row_ptr, 0, sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(st.edge_off, 0, sizeof(int) * (n_events + 1), s) != cudaSuccess)
+            return FRNN_ERR_CUDA;
+        p->last = *out;
+        return FRNN_OK;
+    }
+    // stage the per-call header and event table
+    const int slot = p->ring_pos;
+    p->ring_pos = (p->ring_pos + 1) % kRing;
+    if (cudaEventSynchronize(p->ring_ev[slot]) != cudaSuccess) return FRNN_ERR_CUDA;
+    CallHdr* h = reinterpret_cast<CallHdr*>(p->h_call[slot]);
+    EvDesc* ev = reinterpret_cast<EvDesc*>(p->h_call[slot] + sizeof(CallHdr));
+    const int cpp = p->prm.cells_per_point;
+    int chunks = 0;
+    for (int b = 0; b < n_events; ++b) {
+        const long long nb = ev_off[b + 1] - ev_off[b];
+        const int nc = nb > 0 ? (int)((nb + kChunk - 1) / kChunk) : 1;
+        ev[b].pt_off = ev_off[b];
+        ev[b].n = (int)nb;
+        ev[b].chunk_off = chunks;
+        ev[b].nchunk = nc;
+        ev[b].cell_budget = (int)(cpp * nb + 4096);
+        ev[b].pad0 = ev[b].pad1 = 0;
+        chunks += nc;
+    }
+    h->emb = emb;
+    h->n_total = n_total;
+    h->n_events = n_events;
+    h->total_chunks = chunks;
+    h->d = d;
+    h->dp = (d + 3) & ~3;
+    h->k = k;
+    h->r = r;
+    h->r2 = r * r;
+    h->g_max = p->tuning.g_max;
+    h->cell_scale = p->tuning.cell_scale;
+    h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
+    h->edge_capacity = p->edge_cap;
+    const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
+    if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FRNN_ERR_CUDA;
+    if (cudaEventRecord(p->ring_ev[slot], s) != cudaSuccess) return FRNN_ERR_CUDA;
+    const int cap = next_pow2((k > 32 ? k : 32) + 32);
+    rc = launch(p, h->dp / 4, cap, s, stage_ev);
+    if (rc != FRNN_OK) return rc;
+    p->last = *out;
+    return FRNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int frnn_version(void) { return kVersion; }
+
+const char* frnn_status_string(int status)
+{
+    switch (status) {
+        case FRNN_OK: return "ok";
+        case FRNN_ERR_INVALID_ARG: return "invalid argument";
+        case FRNN_ERR_CUDA: return "CUDA runtime error";
+        case FRNN_ERR_OOM: return "device out of memory";
+        case FRNN_ERR_NONFINITE_INPUT: return "input holds NaN or Inf; that event's rows are empty";
+        case FRNN_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+        case FRNN_ERR_OVERFLOW: return "edges exceed the edge capacity";
+        case FRNN_ERR_CAPACITY: return "call exceeds a plan capacity";
+        default: return "unknown status";
+    }
+}
+
+int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
+{
+    if (!out || !prm) return FRNN_ERR_INVALID_ARG;
+    *out = nullptr;
+    frnn_plan_params q = *prm;
+    if (q.d_max < 1 || q.d_max > kMaxDims || q.n_max < 0 || q.events_max < 1 ||
+        q.k_max_cap < 1 || q.k_max_cap > 1024 || q.edge_capacity < 0 || q.cells_per_point < 0)
+        return FRNN_ERR_INVALID_ARG;
+    if (q.cells_per_point == 0) q.cells_per_point = 4;
+    if (q.edge_capacity == 0) {
+        if (q.n_max * (long long)q.k_max_cap >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+        q.edge_capacity = q.n_max * (long long)q.k_max_cap;
+    }
+    if (q.edge_capacity >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+    const long long cells_max = q.cells_per_point * q.n_max + 4096ll * q.events_max;
+    if (cells_max >= (1ll << 31) || q.n_max >= (1ll << 31) - 1) return FRNN_ERR_INVALID_ARG;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || q.device < 0 || q.device >= n_dev) {
+        cudaGetLastError();
+        return q.device < 0 ? FRNN_ERR_INVALID_ARG : FRNN_ERR_CUDA;
+    }
+    DeviceGuard dg(q.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    frnn_plan* p = new (std::nothrow) frnn_plan();
+    if (!p) return FRNN_ERR_OOM;
+    p->prm = q;
+    p->dp_max = (q.d_max + 3) & ~3;
+    p->cells_max = cells_max;
+    p->edge_cap = q.edge_capacity;
+    p->tiles_cells = (int)((cells_max + kScanTile - 1) / kScanTile) + 1;
+    p->tiles_rows = (int)((q.n_max + kScanTile - 1) / kScanTile) + 1;
+    cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, q.device);
+    int rc = FRNN_OK;
+    DevState& st = p->st;
+    const long long n = q.n_max, ev = q.events_max;
+    p->call_bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)ev;
+#define ALLOC(ptr, cnt) \
+    if (rc == FRNN_OK) rc = plan_alloc(p, &(ptr), (cnt))
+    ALLOC(p->d_call, (long long)p->call_bytes);
+    st.hdr = reinterpret_cast<const CallHdr*>(p->d_call);
+    st.ev = reinterpret_cast<const EvDesc*>(p->d_call + sizeof(CallHdr));
+    ALLOC(st.plan, ev);
+    ALLOC(st.bb_min, ev * kMaxDims);
+    ALLOC(st.bb_max, ev * kMaxDims);
+    ALLOC(st.chunk_done, ev);
+    ALLOC(st.nonfinite, ev);
+    ALLOC(st.counters, (long long)kCtrCount);
+    ALLOC(st.cells_total, 1);
+    ALLOC(st.key, n);
+    ALLOC(st.rank, n);
+    ALLOC(st.perm, n);
+    ALLOC(st.cell_s, n);
+    ALLOC(st.xs, n * p->dp_max);
+    ALLOC(st.deg_s, n);
+    ALLOC(st.cnt_o, n);
+    ALLOC(st.row_ptr, n + 1);
+    ALLOC(st.cell_count, cells_max);
+    ALLOC(st.cell_start, cells_max + 1);
+    ALLOC(st.scan_cells, (long long)p->tiles_cells);
+    ALLOC(st.scan_rows, (long long)p->tiles_rows);
+    ALLOC(st.col, q.edge_capacity);
+    if (q.flags & FRNN_EMIT_D2) ALLOC(st.d2, q.edge_capacity);
+    ALLOC(st.edge_off, ev + 1);
+    ALLOC(st.status, 1);
+#undef ALLOC
+    for (int i = 0; rc == FRNN_OK && i < kRing; ++i) {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&p->h_call[i]), p->call_bytes, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ring_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = FRNN_ERR_OOM;
+    }
+    if (rc == FRNN_OK && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = FRNN_ERR_CUDA;
+    if (rc == FRNN_OK && config_pt(p->n_sm, &p->base_cfg) != 0) rc = FRNN_ERR_CUDA;
+    if (rc == FRNN_OK) {
+        rc = reset_device_state(p, nullptr);
+        if (rc == FRNN_OK && cudaMemset(st.status, 0, sizeof(unsigned)) != cudaSuccess) rc = FRNN_ERR_CUDA;
+        if (rc == FRNN_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FRNN_ERR_CUDA;
+    }
+    if (rc != FRNN_OK) {
+        cudaGetLastError();
+        plan_free_all(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return FRNN_OK;
+}
+
+int frnn_plan_destroy(frnn_plan* p)
+{
+    if (!p) return FRNN_OK;
+    DeviceGuard dg(p->prm.device);
+    cudaDeviceSynchronize();
+    plan_free_all(p);
+    delete p;
+    return FRNN_OK;
+}
+
+int frnn_plan_set_tuning(frnn_plan* p, const frnn_tuning* t)
+{
+    if (!p || !t) return FRNN_ERR_INVALID_ARG;
+    const int g = t->g_max == 0 ? 4 : t->g_max;
+    const float cs = t->cell_scale == 0.f ? 1.0f : t->cell_scale;
+    if (g < 1 || g > kMaxG || !(cs >= 1.0f) || !std::isfinite(cs) || cs > 1e6f) return FRNN_ERR_INVALID_ARG;
+    p->tuning.g_max = g;
+    p->tuning.cell_scale = cs;
+    return FRNN_OK;
+}
+
+int frnn_plan_get_tuning(const frnn_plan* p, frnn_tuning* t)
+{
+    if (!p || !t) return FRNN_ERR_INVALID_ARG;
+    *t = p->tuning;
+    return FRNN_OK;
+}
+
+int frnn_build_graph(frnn_plan* p, const float* emb, int64_t n, int d, float r, int k_max,
+                     void* stream, frnn_csr* out)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    if (n < 0) return FRNN_ERR_INVALID_ARG;
+    const int64_t off[2] = {0, n};
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    return build_batched(p, emb, off, 1, d, r, k_max, static_cast<cudaStream_t>(stream), out);
+}
+
+int frnn_build_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
+                             int d, float r, int k_max, void* stream, frnn_csr* out)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    return build_batched(p, emb, ev_off, n_events, d, r, k_max, static_cast<cudaStream_t>(stream), out);
+}
+
+int frnn_build_graph_profiled(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
+                              int d, float r, int k_max, void* stream, frnn_csr* out, float* stage_ms,
+                              int n_stages)
+{
+    if (!p || !stage_ms || n_stages < kStages) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev[kStages + 1] = {};
+    int rc = FRNN_OK;
+    for (int i = 0; i <= kStages && rc == FRNN_OK; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) rc = FRNN_ERR_CUDA;
+    if (rc == FRNN_OK) rc = build_batched(p, emb, ev_off, n_events, d, r, k_max, s, out, ev);
+    for (int i = 0; i < kStages; ++i) stage_ms[i] = 0.f;
+    if (rc == FRNN_OK && out->n_total > 0) {
+        if (cudaEventSynchronize(ev[kStages]) != cudaSuccess) rc = FRNN_ERR_CUDA;
+        for (int i = 0; rc == FRNN_OK && i < kStages; ++i)
+            if (cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = FRNN_ERR_CUDA;
+    }
+    for (int i = 0; i <= kStages; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+int frnn_get_last_status(frnn_plan* p, void* stream)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    unsigned word = 0;
+    if (cudaMemcpyAsync(&word, p->st.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(p->st.status, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    if (word & kStTimeout) {
+        // a wait gave up part-way: restore the between-builds state
+        reset_device_state(p, s);
+        cudaStreamSynchronize(s);
+        return FRNN_ERR_TIMEOUT;
+    }
+    if (word & kStOverflow) return FRNN_ERR_OVERFLOW;
+    if (word & kStNonfinite) return FRNN_ERR_NONFINITE_INPUT;
+    return FRNN_OK;
+}
+
+int frnn_build_graph_host(frnn_plan* p, const float* h_emb, const int64_t* ev_off, int n_events,
+                          int d, float r, int k_max, int32_t* h_row_ptr, int32_t* h_col,
+                          int64_t col_capacity, int32_t* h_edge_off, int64_t* h_n_edges, void* stream)
+{
+    if (!p || !ev_off || !h_row_ptr || !h_n_edges || col_capacity < 0 || n_events < 1) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = ev_off[n_events];
+    if (n < 0 || (n > 0 && !h_emb) || d < 1 || d > kMaxDims) return FRNN_ERR_INVALID_ARG;
+    if (n > p->prm.n_max || d > p->prm.d_max) return FRNN_ERR_CAPACITY;
+    const long long need = n * d;
+    if (need > p->d_input_floats) {
+        if (p->d_input) {
+            cudaStreamSynchronize(s);
+            cudaFree(p->d_input);
+            p->d_input = nullptr;
+            p->d_input_floats = 0;
+        }
+        const long long want = p->prm.n_max * (long long)p->prm.d_max;
+        if (cudaMalloc(reinterpret_cast<void**>(&p->d_input), sizeof(float) * (size_t)(want > 0 ? want : 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return FRNN_ERR_OOM;
+        }
+        p->d_input_floats = want;
+    }
+    if (n > 0 && cudaMemcpyAsync(p->d_input, h_emb, sizeof(float) * (size_t)need, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FRNN_ERR_CUDA;
+    frnn_csr csr;
+    int rc = build_batched(p, p->d_input, ev_off, n_events, d, r, k_max, s, &csr);
+    if (rc != FRNN_OK) return rc;
+    if (cudaMemcpyAsync(h_row_ptr, csr.row_ptr, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FRNN_ERR_CUDA;
+    if (h_edge_off && cudaMemcpyAsync(h_edge_off, csr.edge_off, sizeof(int32_t) * (size_t)(n_events + 1),
+                                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FRNN_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FRNN_ERR_CUDA;
+    const long long e = h_row_ptr[n];
+    *h_n_edges = e;
+    rc = FRNN_OK;
+    if (e > col_capacity || (e > 0 && !h_col)) {
+        rc = FRNN_ERR_OVERFLOW;
+    } else if (e > 0) {
+        if (cudaMemcpyAsync(h_col, csr.col, sizeof(int32_t) * (size_t)e, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return FRNN_ERR_CUDA;
+    }
+    const int st = frnn_get_last_status(p, stream);
+    return st != FRNN_OK ? st : rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal data structures shared by the kernels and the host side of libfrnn.
+#pragma once
+
+#include <cstdint>
+
+namespace frnn {
+
+constexpr int kMaxG = 4;            // most hashed (gridded) dimensions
+constexpr int kMaxDims = 64;        // largest embedding dimension
+constexpr int kChunk = 2048;        // points per chunk of the per-point kernels
+constexpr int kPtThreads = 256;     // threads of the per-point kernels
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kWalkThreads = 256;   // 8 warps, one query per warp at a time
+constexpr int kMaxDimCells = 32768; // cells along one hashed dimension (float32 key bound)
+
+// Bits of the device status word (1 << frnn_status).
+constexpr unsigned kStNonfinite = 1u << 4;
+constexpr unsigned kStTimeout = 1u << 5;
+constexpr unsigned kStOverflow = 1u << 6;
+
+// Written by the host once per call and uploaded in front of the event table.
+struct CallHdr {
+    const float* emb;    // device [n_total][d], caller-owned
+    long long n_total;   // points of the call
+    int n_events;
+    int total_chunks;    // sum over events of max(1, ceil(n_b / kChunk))
+    int d;
+    int dp;              // row length of the sorted copy (d rounded up to 4)
+    int k;               // neighbour cap
+    float r;
+    float r2;            // fl32(r * r)
+    int g_max;           // tuning: most hashed dims
+    float cell_scale;    // tuning: cell edge / r (>= 1)
+    int emit_d2;
+    long long edge_capacity;
+};
+
+struct EvDesc {
+    long long pt_off;    // first point of the event within the call
+    int n;               // points
+    int chunk_off;       // first chunk of the event
+    int nchunk;          // chunks (>= 1, also for an empty event)
+    int cell_budget;     // cell slots the event may use
+    int pad0, pad1;
+};
+
+// Written on the device by the planning step (one per event).
+struct EvPlan {
+    float lo[kMaxG];     // lower corner of the grid along each hashed dim
+    float s;             // cell edge
+    float inv_s;         // fl32(1 / s)
+    int g;               // hashed dims (>= 1)
+    int skip;            // 1: the event holds a non-finite value, rows are left empty
+    int dims[kMaxG];     // which embedding dims are hashed (widest first)
+    int ncell[kMaxG];
+    int stride[kMaxG];   // linear cell id = sum k_t * stride_t; dims[g-1] is fastest
+    int n_cells;
+    int cell_off;        // first global cell slot of the event
+};
+
+// Counter slots (all return to zero at the end of every build).
+enum { kCtrPlanned = 0, kCtrScanCellsTile, kCtrScanCellsExit, kCtrScanRowsTile,
+       kCtrScanRowsExit, kCtrCount = 8 };
+
+// Device pointers owned by the plan.  Fixed for the plan's life, so a
+// captured CUDA graph of the build stays valid for every call: everything
+// that changes per call is read from *hdr and ev[].
+struct DevState {
+    const CallHdr* hdr;
+    const EvDesc* ev;
+    EvPlan* plan;
+    unsigned* bb_min;        // [events_max * kMaxDims] order-preserving encodings
+    unsigned* bb_max;
+    unsigned* chunk_done;    // [events_max]
+    unsigned* nonfinite;     // [events_max]
+    unsigned* counters;      // [kCtrCount]
+    int* cells_total;
+    unsigned* key;           // [n_max] cell id of each input point (event-local)
+    unsigned* rank;          // [n_max] slot of the point inside its cell
+    int* perm;               // [n_max] sorted position -> event-local point index
+    unsigned* cell_s;        // [n_max] sorted position -> cell id
+    float* xs;               // [n_max * dp_max] points in cell order, rows padded with 0
+    int* deg_s;              // [n_max] sorted position -> |S_i|
+    int* cnt_o;              // [n_max] point -> min(|S_i|, k)
+    int* row_ptr;            // [n_max + 1]
+    unsigned* cell_count;    // [cells_max], zero between builds
+    int* cell_start;         // [cells_max + 1]
+    unsigned long long* scan_cells;  // [tiles], zero between builds
+    unsigned long long* scan_rows;
+    int* col;
+    float* d2;
+    int* edge_off;           // [events_max + 1]
+    unsigned* status;
+};
+
+struct LaunchCfg {
+    int grid_pt;       // per-point kernels (persistent: blocks loop over chunks)
+    int grid_scan;     // scans (persistent: blocks take tiles from a counter)
+    int grid_count;    // count walk (persistent: warps stride over queries)
+    int grid_fill;     // fill walk
+    int fill_cap;      // per-warp key buffer of the fill walk (power of two, >= k + 32)
+    int fill_smem;     // its dynamic shared memory in bytes
+};
+
+// Host-side launchers (frnn_kernels.cu).  All return a cudaError_t value.
+// stage_events: NULL, or kStages + 1 cudaEvent_t recorded around the stages.
+constexpr int kStages = 7;
+int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream, void* stage_events);
+int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg);
+int config_pt(int n_sm, LaunchCfg* cfg);
+
+}  // namespace frnn

@@ -1,0 +1,889 @@
+// Kernels of the fixed-radius nearest-neighbour graph build (sm_103a).
+//
+// One build is seven persistent launches on one stream.  Every size is read
+// from the per-call header in device memory, so the launch shapes depend only
+// on the GPU and a captured CUDA graph replays any call within the plan's
+// capacities.  All stages work on a batch of events (a single event is a
+// batch of one):
+//
+//   1 k_bbox_plan   per-event bounding box; the last chunk of an event picks
+//                   its cell grid (hashed dims, cell edge, strides); the last
+//                   event planned lays the events' cell tables end to end
+//   2 k_key_hist    cell id of every point, histogram by atomics (the old
+//                   count is the point's slot inside its cell)
+//   3 k_scan<0>     exclusive scan of the cell histogram (decoupled look-back),
+//                   which also clears the histogram for the next build
+//   4 k_scatter     points copied into cell order, rows padded to a multiple
+//                   of four floats for 16-byte loads
+//   5 k_walk_count  one warp per query: walk the 3^(g-1) runs of neighbouring
+//                   cells, count the points within r (the degree |S_i|)
+//   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr
+//   7 k_walk_fill   the same walk again, keeping the k smallest (d2, j) keys,
+//                   written to col in increasing order
+//
+// Paper: Sec. 3.4 (fixed-radius neighbours by a grid of cells, cost growing
+// as 3^g with the gridded dimensions g, which is why at most four are used)
+// and Sec. 3.1 (the k nearest within the radius).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "frnn_internal.h"
+
+namespace frnn {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kCellMargin = 1.0f + 1.0f / 64.0f;  // cell edge >= r * (1 + 2^-6)
+constexpr int kSpinLimit = 1 << 22;                 // bounded waits in the scans
+
+// Order-preserving map float -> uint32 (for atomicMin / atomicMax).
+__device__ __forceinline__ unsigned f2ord(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int event_of_chunk(const EvDesc* ev, int n_events, int c)
+{
+    int lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ev[mid].chunk_off <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Largest event b with pt_off <= p (empty events share the next one's offset
+// and therefore never win).
+__device__ __forceinline__ int event_of_point(const EvDesc* ev, int n_events, long long p)
+{
+    int lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ev[mid].pt_off <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
+// Returns the thread's exclusive prefix; *total receives the block sum.
+__device__ unsigned block_excl_scan(unsigned v, unsigned* total)
+{
+    __shared__ unsigned s_w[32];
+    __shared__ unsigned s_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    const unsigned incl = warp_incl_scan(v, lane);
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned w = (lane < nw) ? s_w[lane] : 0u;
+        const unsigned wi = warp_incl_scan(w, lane);
+        if (lane < nw) s_w[lane] = wi - w;
+        if (lane == 31) s_tot = wi;
+    }
+    __syncthreads();
+    const unsigned r = s_w[warp] + incl - v;
+    *total = s_tot;
+    __syncthreads();
+    return r;
+}
+
+// --------------------------------------------------------------------------
+// Stage 1: bounding box + per-event plan.
+
+// Pick the event's cell grid from its bounding box.  Called by the block that
+// finished the event's last chunk, after a fence.  Correctness never depends
+// on the choice: any grid whose cell edge is at least r (with the margin the
+// float32 key arithmetic needs) finds every neighbour.
+__device__ void plan_event(const DevState& st, const CallHdr& h, int b, const EvDesc& e)
+{
+    __shared__ float s_w[kMaxDims];
+    __shared__ float s_lo[kMaxDims];
+    const int D = h.d;
+    for (int t = threadIdx.x; t < D; t += blockDim.x) {
+        const float lo = ord2f(__ldcg(&st.bb_min[b * kMaxDims + t]));
+        const float hi = ord2f(__ldcg(&st.bb_max[b * kMaxDims + t]));
+        s_lo[t] = lo;
+        s_w[t] = hi - lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        EvPlan pl;
+        for (int t = 0; t < kMaxG; ++t) {
+            pl.lo[t] = 0.f; pl.dims[t] = 0; pl.ncell[t] = 1; pl.stride[t] = 0;
+        }
+        pl.g = 1;
+        pl.stride[0] = 1;
+        pl.n_cells = 1;
+        pl.cell_off = 0;
+        pl.s = h.r;
+        pl.inv_s = 1.0f / h.r;
+        pl.skip = __ldcg(&st.nonfinite[b]) ? 1 : 0;
+        if (!pl.skip && e.n > 0) {
+            // widest dims first (ties: lower index)
+            int picks[kMaxG];
+            const int npick = min(min(h.g_max, kMaxG), D);
+            unsigned long long used = 0ull;
+            for (int i = 0; i < npick; ++i) {
+                int best = -1;
+                float bw = -1.f;
+                for (int t = 0; t < D; ++t) {
+                    if ((used >> t) & 1ull) continue;
+                    if (s_w[t] > bw) { bw = s_w[t]; best = t; }
+                }
+                picks[i] = best;
+                used |= 1ull << best;
+            }
+            float s = h.r * h.cell_scale * kCellMargin;
+            const int maxc0 = min(e.cell_budget, kMaxDimCells);
+            const float w0 = s_w[picks[0]];
+            if (w0 / s > (float)(maxc0 - 3)) s = (w0 / (float)(maxc0 - 3)) * kCellMargin;
+            int g = 0;
+            long long cells = 1;
+            for (int i = 0; i < npick; ++i) {
+                const int t = picks[i];
+                const float a = s_w[t] / s;
+                const int nc = (a >= (float)(kMaxDimCells - 1)) ? kMaxDimCells : (int)a + 1;
+                if (g > 0 && nc < 4) break;
+                if (g > 0 && cells * nc > (long long)e.cell_budget) break;
+                pl.dims[g] = t;
+                pl.ncell[g] = nc;
+                pl.lo[g] = s_lo[t];
+                cells *= nc;
+                ++g;
+            }
+            pl.g = g;
+            pl.stride[g - 1] = 1;
+            for (int t = g - 2; t >= 0; --t) pl.stride[t] = pl.stride[t + 1] * pl.ncell[t + 1];
+            pl.n_cells = (int)cells;
+            pl.s = s;
+            pl.inv_s = 1.0f / s;
+        }
+        st.plan[b] = pl;
+    }
+    __syncthreads();
+    // leave the per-event accumulators ready for the next build
+    for (int t = threadIdx.x; t < D; t += blockDim.x) {
+        st.bb_min[b * kMaxDims + t] = 0xffffffffu;
+        st.bb_max[b * kMaxDims + t] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        st.chunk_done[b] = 0u;
+        st.nonfinite[b] = 0u;
+    }
+}
+
+// The last event to be planned lays the cell tables of all events end to end.
+__device__ void place_cell_tables(const DevState& st, int n_events)
+{
+    unsigned carry = 0;
+    for (int base = 0; base < n_events; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        const unsigned v = (b < n_events) ? (unsigned)__ldcg(&st.plan[b].n_cells) : 0u;
+        unsigned tot;
+        const unsigned ex = block_excl_scan(v, &tot);
+        if (b < n_events) st.plan[b].cell_off = (int)(carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *st.cells_total = (int)carry;
+        st.counters[kCtrPlanned] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
+{
+    __shared__ unsigned s_min[kMaxDims], s_max[kMaxDims];
+    __shared__ int s_nf, s_last, s_last_planner;
+    const CallHdr h = *st.hdr;
+    const int D = h.d;
+    for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
+        const int b = event_of_chunk(st.ev, h.n_events, c);
+        const EvDesc e = st.ev[b];
+        for (int t = threadIdx.x; t < D; t += blockDim.x) {
+            s_min[t] = 0xffffffffu;
+            s_max[t] = 0u;
+        }
+        if (threadIdx.x == 0) s_nf = 0;
+        __syncthreads();
+        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long rem = (long long)e.n - first;
+        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        const float* base = h.emb + (e.pt_off + first) * D;
+        const int nel = np * D;
+        bool nf = false;
+        if ((kPtThreads % D) == 0) {
+            // every element this thread reads belongs to dim threadIdx.x % D
+            unsigned lmin = 0xffffffffu, lmax = 0u;
+            for (int i = threadIdx.x; i < nel; i += kPtThreads) {
+                const float v = __ldg(base + i);
+                nf |= !isfinite(v);
+                const unsigned u = f2ord(v);
+                lmin = min(lmin, u);
+                lmax = max(lmax, u);
+            }
+            if (threadIdx.x < nel) {
+                atomicMin(&s_min[threadIdx.x % D], lmin);
+                atomicMax(&s_max[threadIdx.x % D], lmax);
+            }
+        } else {
+            for (int i = threadIdx.x; i < nel; i += kPtThreads) {
+                const float v = __ldg(base + i);
+                nf |= !isfinite(v);
+                const unsigned u = f2ord(v);
+                atomicMin(&s_min[i % D], u);
+                atomicMax(&s_max[i % D], u);
+            }
+        }
+        if (nf) s_nf = 1;
+        __syncthreads();
+        if (np > 0) {
+            for (int t = threadIdx.x; t < D; t += blockDim.x) {
+                atomicMin(&st.bb_min[b * kMaxDims + t], s_min[t]);
+                atomicMax(&st.bb_max[b * kMaxDims + t], s_max[t]);
+            }
+        }
+        if (threadIdx.x == 0 && s_nf) atomicOr(&st.nonfinite[b], 1u);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned done = atomicAdd(&st.chunk_done[b], 1u);
+            s_last = (done == (unsigned)e.nchunk - 1u);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            plan_event(st, h, b, e);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (st.plan[b].skip) atomicOr(st.status, kStNonfinite);
+                __threadfence();
+                const unsigned pl = atomicAdd(&st.counters[kCtrPlanned], 1u);
+                s_last_planner = (pl == (unsigned)h.n_events - 1u);
+            }
+            __syncthreads();
+            if (s_last_planner) {
+                __threadfence();
+                place_cell_tables(st, h.n_events);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------
+// Stage 2: cell id and histogram.
+
+// Cell coordinate along one hashed dim.  a = (x - lo) * inv_s in float32 has a
+// relative error of at most ~3 * 2^-24; with at most 2^15 cells per dim and a
+// cell edge of at least r * (1 + 2^-6), two points whose float32 d2 passes the
+// radius test land in cells at most one apart along every hashed dim.
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv_s, int ncell)
+{
+    const float a = __fmul_rn(__fsub_rn(x, lo), inv_s);
+    return (a < (float)ncell) ? (int)a : ncell - 1;  // a >= 0: truncation is floor
+}
+
+__global__ void __launch_bounds__(kPtThreads) k_key_hist(DevState st)
+{
+    const CallHdr h = *st.hdr;
+    const int D = h.d;
+    for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
+        const int b = event_of_chunk(st.ev, h.n_events, c);
+        const EvDesc e = st.ev[b];
+        const EvPlan pl = st.plan[b];
+        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long rem = (long long)e.n - first;
+        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        for (int i = threadIdx.x; i < np; i += kPtThreads) {
+            const long long p = e.pt_off + first + i;
+            const float* x = h.emb + p * D;
+            unsigned cid = 0;
+            if (!pl.skip) {
+#pragma unroll
+                for (int t = 0; t < kMaxG; ++t) {
+                    if (t < pl.g)
+                        cid += (unsigned)(cell_coord(__ldg(x + pl.dims[t]), pl.lo[t], pl.inv_s,
+                                                     pl.ncell[t]) * pl.stride[t]);
+                }
+            }
+            st.key[p] = cid;
+            st.rank[p] = atomicAdd(&st.cell_count[pl.cell_off + cid], 1u);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Stages 3 and 6: exclusive scan with decoupled look-back.
+//
+// Tiles are taken from a counter in increasing order, so a tile only ever
+// waits for tiles already taken by running blocks; every wait is bounded and
+// latches FRNN_ERR_TIMEOUT instead of hanging.  The block that exits last
+// clears the tile states and counters for the next build.
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+
+__device__ unsigned lookback(unsigned long long* state, int tile, int lane, unsigned* status)
+{
+    unsigned prefix = 0;
+    int top = tile - 1;
+    for (;;) {
+        const int idx = top - lane;
+        unsigned long long s = 0;
+        int spins = 0;
+        for (;;) {
+            s = (idx >= 0) ? ld_relaxed(state + idx) : kFlagPre;
+            if (__all_sync(kFull, (s >> 62) != 0)) break;
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicOr(status, kStTimeout);
+                return prefix;
+            }
+            __nanosleep(32);
+        }
+        const unsigned pmask = __ballot_sync(kFull, (s >> 62) == 2);
+        const unsigned v = (unsigned)s;
+        if (pmask) {
+            const int first = __ffs(pmask) - 1;
+            prefix += warp_sum(lane <= first ? v : 0u);
+            return prefix;
+        }
+        prefix += warp_sum(v);
+        top -= 32;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
+{
+    __shared__ int s_tile;
+    __shared__ unsigned s_prefix;
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long M;
+    unsigned* in;
+    int* out;
+    unsigned long long* state;
+    unsigned* tile_ctr;
+    unsigned* exit_ctr;
+    if (MODE == 0) {
+        M = *st.cells_total;
+        in = st.cell_count;
+        out = st.cell_start;
+        state = st.scan_cells;
+        tile_ctr = &st.counters[kCtrScanCellsTile];
+        exit_ctr = &st.counters[kCtrScanCellsExit];
+    } else {
+        M = st.hdr->n_total;
+        in = reinterpret_cast<unsigned*>(st.cnt_o);
+        out = st.row_ptr;
+        state = st.scan_rows;
+        tile_ctr = &st.counters[kCtrScanRowsTile];
+        exit_ctr = &st.counters[kCtrScanRowsExit];
+    }
+    const int ntiles = (int)((M + kScanTile - 1) / kScanTile);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntiles) break;
+        const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+        unsigned v[kScanItems];
+        if (base + kScanItems <= M) {
+            const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+            const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            if (MODE == 0) {
+                *reinterpret_cast<uint4*>(in + base) = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4*>(in + base + 4) = make_uint4(0, 0, 0, 0);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kScanItems; ++i) {
+                v[i] = (base + i < M) ? in[base + i] : 0u;
+                if (MODE == 0 && base + i < M) in[base + i] = 0u;
+            }
+        }
+        unsigned tsum = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) tsum += v[i];
+        unsigned total;
+        const unsigned texcl = block_excl_scan(tsum, &total);
+        if (warp == 0) {
+            unsigned prefix = 0;
+            if (tile == 0) {
+                if (lane == 0) st_relaxed(state, kFlagPre | total);
+            } else {
+                if (lane == 0) st_relaxed(state + tile, kFlagAgg | total);
+                prefix = lookback(state, tile, lane, st.status);
+                if (lane == 0) st_relaxed(state + tile, kFlagPre | (unsigned)(prefix + total));
+            }
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        unsigned run = s_prefix + texcl;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            if (base + i < M) out[base + i] = (int)run;
+            run += v[i];
+        }
+        __syncthreads();
+    }
+    // exit: the last block out restores the zero state
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned e = atomicAdd(exit_ctr, 1u);
+        s_last = (e == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const unsigned last_incl = ntiles > 0 ? (unsigned)ld_relaxed(state + ntiles - 1) : 0u;
+    if (threadIdx.x == 0) {
+        out[M] = (int)last_incl;
+        *tile_ctr = 0u;
+        *exit_ctr = 0u;
+    }
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
+    if (MODE == 1) {
+        // per-event edge offsets, and the capacity check of the fill walk
+        const int B = st.hdr->n_events;
+        for (int b = threadIdx.x; b <= B; b += blockDim.x) {
+            const long long p = (b < B) ? st.ev[b].pt_off : M;
+            st.edge_off[b] = (p == M) ? (int)last_incl : __ldcg(&out[p]);
+        }
+        if (threadIdx.x == 0 && (long long)last_incl > st.hdr->edge_capacity)
+            atomicOr(st.status, kStOverflow);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Stage 4: scatter into cell order.
+
+__global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
+{
+    const CallHdr h = *st.hdr;
+    const int D = h.d, dp = h.dp;
+    const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
+    for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
+        const int b = event_of_chunk(st.ev, h.n_events, c);
+        const EvDesc e = st.ev[b];
+        const int cell_off = st.plan[b].cell_off;
+        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long rem = (long long)e.n - first;
+        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        for (int i = threadIdx.x; i < np; i += kPtThreads) {
+            const long long p = e.pt_off + first + i;
+            const unsigned cid = st.key[p];
+            const long long pos = (long long)st.cell_start[cell_off + cid] + st.rank[p];
+            st.perm[pos] = (int)(first + i);
+            st.cell_s[pos] = cid;
+            const float* x = h.emb + p * D;
+            float4* dst = reinterpret_cast<float4*>(st.xs + pos * dp);
+            if (vec) {
+                const float4* src = reinterpret_cast<const float4*>(x);
+                for (int t = 0; t < dp / 4; ++t) dst[t] = __ldg(src + t);
+            } else {
+                for (int t = 0; t < dp; t += 4) {
+                    float4 w;
+                    w.x = (t + 0 < D) ? __ldg(x + t + 0) : 0.f;
+                    w.y = (t + 1 < D) ? __ldg(x + t + 1) : 0.f;
+                    w.z = (t + 2 < D) ? __ldg(x + t + 2) : 0.f;
+                    w.w = (t + 3 < D) ? __ldg(x + t + 3) : 0.f;
+                    dst[t / 4] = w;
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Stages 5 and 7: the neighbour-cell walk.
+
+// Squared distance in float32, dims added in order 0, 1, ..., one rounding per
+// operation (no fused multiply-add).  Padding dims are 0 on both sides and add
+// exactly 0, so the value equals the unpadded sequential sum.
+template <int DP4>
+__device__ __forceinline__ float dist2(const float4 (&q)[DP4], const float4* row)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < DP4; ++c) {
+        const float4 v = __ldg(row + c);
+        float d;
+        d = __fsub_rn(q[c].x, v.x); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(q[c].y, v.y); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(q[c].z, v.z); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(q[c].w, v.w); s = __fadd_rn(s, __fmul_rn(d, d));
+    }
+    return s;
+}
+
+// Per-warp cache of the current event (a warp's queries mostly stay in one).
+struct WalkEvent {
+    long long lo, hi, pt_off;
+    EvPlan pl;
+};
+
+__device__ __forceinline__ void walk_event(const DevState& st, int n_events, long long q, WalkEvent& we)
+{
+    if (q >= we.lo && q < we.hi) return;
+    const int b = event_of_point(st.ev, n_events, q);
+    we.pt_off = st.ev[b].pt_off;
+    we.lo = we.pt_off;
+    we.hi = we.pt_off + st.ev[b].n;
+    we.pl = st.plan[b];
+}
+
+// Lane l < 3^(g-1) takes one combination of offsets {-1,0,1} along the g-1
+// slower hashed dims; along the fastest dim the three cells k-1..k+1 are
+// adjacent in memory, so each combination is one contiguous run of points.
+__device__ __forceinline__ void walk_runs(const EvPlan& pl, unsigned cid, const int* cell_start,
+                                          int lane, int& beg, int& len)
+{
+    int k[kMaxG];
+#pragma unroll
+    for (int t = 0; t < kMaxG; ++t) k[t] = (t < pl.g) ? (int)((cid / (unsigned)pl.stride[t]) % (unsigned)pl.ncell[t]) : 0;
+    int nr = 1;
+#pragma unroll
+    for (int t = 0; t < kMaxG - 1; ++t) if (t < pl.g - 1) nr *= 3;
+    beg = 0;
+    len = 0;
+    if (lane < nr) {
+        int rem = lane, cbase = 0;
+        bool ok = true;
+#pragma unroll
+        for (int t = 0; t < kMaxG - 1; ++t) {
+            if (t < pl.g - 1) {
+                const int kt = k[t] + (rem % 3) - 1;
+                rem /= 3;
+                ok &= (kt >= 0) && (kt < pl.ncell[t]);
+                cbase += kt * pl.stride[t];
+            }
+        }
+        if (ok) {
+            int kl = 0, ncl = 1;
+#pragma unroll
+            for (int t = 0; t < kMaxG; ++t) {
+                if (t == pl.g - 1) {
+                    kl = k[t];
+                    ncl = pl.ncell[t];
+                }
+            }
+            const int c0 = cbase + max(kl - 1, 0);
+            const int c1 = cbase + min(kl + 1, ncl - 1);
+            beg = cell_start[pl.cell_off + c0];
+            len = cell_start[pl.cell_off + c1 + 1] - beg;
+        }
+    }
+}
+
+// Index of the run holding candidate qi: the smallest r with incl[r] > qi,
+// by binary lifting over the lanes' inclusive prefix sums.
+__device__ __forceinline__ int find_run(int incl, int qi)
+{
+    int r = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(kFull, incl, r + step - 1);
+        if (v <= qi) r += step;
+    }
+    return r;
+}
+
+template <int DP4>
+__global__ void __launch_bounds__(kWalkThreads) k_walk_count(DevState st)
+{
+    const int lane = threadIdx.x & 31;
+    const long long P = st.hdr->n_total;
+    const float r2 = st.hdr->r2;
+    const int K = st.hdr->k;
+    const int B = st.hdr->n_events;
+    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
+    WalkEvent we;
+    we.lo = 1;
+    we.hi = 0;
+    for (long long q = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); q < P; q += nwarps) {
+        walk_event(st, B, q, we);
+        int deg = 0;
+        if (!we.pl.skip) {
+            float4 qv[DP4];
+#pragma unroll
+            for (int c = 0; c < DP4; ++c) qv[c] = __ldg(xs4 + q * DP4 + c);
+            int beg, len;
+            walk_runs(we.pl, __ldg(st.cell_s + q), st.cell_start, lane, beg, len);
+            const int incl = warp_incl_scan(len, lane);
+            const int excl = incl - len;
+            const int T = __shfl_sync(kFull, incl, 31);
+            for (int base = 0; base < T; base += 32) {
+                const int qi = base + lane;
+                const int r = find_run(incl, qi);
+                const int rb = __shfl_sync(kFull, beg, r);
+                const int re = __shfl_sync(kFull, excl, r);
+                bool hit = false;
+                if (qi < T) {
+                    const int cand = rb + (qi - re);
+                    const float d2 = dist2<DP4>(qv, xs4 + (long long)cand * DP4);
+                    hit = (d2 <= r2) && ((long long)cand != q);
+                }
+                deg += __popc(__ballot_sync(kFull, hit));
+            }
+        }
+        if (lane == 0) {
+            st.deg_s[q] = deg;
+            st.cnt_o[we.pt_off + __ldg(st.perm + q)] = min(deg, K);
+        }
+    }
+}
+
+// Warp-wide ascending bitonic sort of one 64-bit key per lane.
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, v, j);
+            const bool up = (lane & k) == 0;
+            const bool lower = (lane & j) == 0;
+            v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
+        }
+    }
+    return v;
+}
+
+// Ascending bitonic sort of buf[0..n) by one warp (pads to a power of two <= cap).
+__device__ void warp_sort_smem(unsigned long long* buf, int n, int lane)
+{
+    int p2 = 32;
+    while (p2 < n) p2 <<= 1;
+    for (int i = n + lane; i < p2; i += 32) buf[i] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < (p2 >> 1); t += 32) {
+                const int i = 2 * j * (t / j) + (t % j);
+                const int l = i + j;
+                const unsigned long long x = buf[i], y = buf[l];
+                const bool up = (i & k) == 0;
+                if ((x > y) == up) {
+                    buf[i] = y;
+                    buf[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int DP4>
+__global__ void __launch_bounds__(kWalkThreads) k_walk_fill(DevState st, int cap)
+{
+    extern __shared__ unsigned long long s_keys[];
+    const int lane = threadIdx.x & 31;
+    unsigned long long* buf = s_keys + (size_t)(threadIdx.x >> 5) * cap;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long P = st.hdr->n_total;
+    const float r2 = st.hdr->r2;
+    const int K = st.hdr->k;
+    const int B = st.hdr->n_events;
+    const int emit = st.hdr->emit_d2;
+    const long long ecap = st.hdr->edge_capacity;
+    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
+    WalkEvent we;
+    we.lo = 1;
+    we.hi = 0;
+    for (long long q = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); q < P; q += nwarps) {
+        walk_event(st, B, q, we);
+        if (we.pl.skip) continue;
+        const long long p = we.pt_off + __ldg(st.perm + q);
+        const int rs = st.row_ptr[p];
+        const int re = st.row_ptr[p + 1];
+        const int cnt = re - rs;
+        if (cnt <= 0) continue;
+        if ((long long)re > ecap) continue;  // OVERFLOW was latched by the row scan
+        float4 qv[DP4];
+#pragma unroll
+        for (int c = 0; c < DP4; ++c) qv[c] = __ldg(xs4 + q * DP4 + c);
+        int beg, len;
+        walk_runs(we.pl, __ldg(st.cell_s + q), st.cell_start, lane, beg, len);
+        const int incl = warp_incl_scan(len, lane);
+        const int excl = incl - len;
+        const int T = __shfl_sync(kFull, incl, 31);
+        unsigned long long thr = ~0ull;
+        int nh = 0;
+        for (int base = 0; base < T; base += 32) {
+            const int qi = base + lane;
+            const int r = find_run(incl, qi);
+            const int rb = __shfl_sync(kFull, beg, r);
+            const int rx = __shfl_sync(kFull, excl, r);
+            unsigned long long key = ~0ull;
+            bool take = false;
+            if (qi < T) {
+                const int cand = rb + (qi - rx);
+                const float d2 = dist2<DP4>(qv, xs4 + (long long)cand * DP4);
+                if ((d2 <= r2) && ((long long)cand != q)) {
+                    key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__ldg(st.perm + cand);
+                    take = key < thr;
+                }
+            }
+            unsigned m = __ballot_sync(kFull, take);
+            if (m == 0u) continue;
+            if (nh + 32 > cap) {
+                // only reached when |S_i| > k: keep the k smallest so far
+                warp_sort_smem(buf, nh, lane);
+                nh = K;
+                thr = buf[K - 1];
+                take = take && (key < thr);
+                m = __ballot_sync(kFull, take);
+            }
+            if (take) buf[nh + __popc(m & lt_mask)] = key;
+            nh += __popc(m);
+            __syncwarp();
+        }
+        const int nout = min(cnt, nh);
+        if (nh <= 32) {
+            unsigned long long v = (lane < nh) ? buf[lane] : ~0ull;
+            v = warp_sort32(v, lane);
+            if (lane < nout) {
+                st.col[rs + lane] = (int)(unsigned)v;
+                if (emit) st.d2[rs + lane] = __uint_as_float((unsigned)(v >> 32));
+            }
+        } else {
+            warp_sort_smem(buf, nh, lane);
+            for (int e2 = lane; e2 < nout; e2 += 32) {
+                const unsigned long long v = buf[e2];
+                st.col[rs + e2] = (int)(unsigned)v;
+                if (emit) st.d2[rs + e2] = __uint_as_float((unsigned)(v >> 32));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Stage boundaries: ev[i] is recorded before stage i and ev[7] after the last
+// (all NULL for an untimed build).
+inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
+{
+    if (ev) cudaEventRecord(ev[i], s);
+}
+
+template <int DP4>
+cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t s, cudaEvent_t* ev)
+{
+    mark(ev, 4, s);
+    k_walk_count<DP4><<<cfg.grid_count, kWalkThreads, 0, s>>>(st);
+    mark(ev, 5, s);
+    k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
+    mark(ev, 6, s);
+    k_walk_fill<DP4><<<cfg.grid_fill, kWalkThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
+    mark(ev, 7, s);
+    return cudaGetLastError();
+}
+
+template <int DP4>
+cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
+{
+    const int smem = (kWalkThreads / 32) * fill_cap * (int)sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_fill<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int nb_c = 0, nb_f = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_count<DP4>, kWalkThreads, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_fill<DP4>, kWalkThreads, smem);
+    if (e != cudaSuccess) return e;
+    cfg->grid_count = n_sm * (nb_c > 0 ? nb_c : 1);
+    cfg->grid_fill = n_sm * (nb_f > 0 ? nb_f : 1);
+    cfg->fill_cap = fill_cap;
+    cfg->fill_smem = smem;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+#define FRNN_DP4_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream, void* stage_events)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(stage_events);
+    mark(ev, 0, s);
+    k_bbox_plan<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    mark(ev, 1, s);
+    k_key_hist<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    mark(ev, 2, s);
+    k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
+    mark(ev, 3, s);
+    k_scatter<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    switch (dp4) {
+#define FRNN_CASE(n) case n: return (int)launch_walks<n>(st, cfg, s, ev);
+        FRNN_DP4_CASES(FRNN_CASE)
+#undef FRNN_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg)
+{
+    switch (dp4) {
+#define FRNN_CASE(n) case n: return (int)config_walks<n>(fill_cap, n_sm, cfg);
+        FRNN_DP4_CASES(FRNN_CASE)
+#undef FRNN_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int config_pt(int n_sm, LaunchCfg* cfg)
+{
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_key_hist, kPtThreads, 0);
+    if (e != cudaSuccess) return (int)e;
+    cfg->grid_pt = n_sm * (nb > 0 ? (nb < 4 ? nb : 4) : 1);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<0>, kScanThreads, 0);
+    if (e != cudaSuccess) return (int)e;
+    cfg->grid_scan = n_sm * (nb > 0 ? (nb < 4 ? nb : 4) : 1);
+    return (int)cudaSuccess;
+}
+
+}  // namespace frnn

@@ -1,0 +1,67 @@
+"""The C ABI without a GPU: the library loads, exports every function the
+header declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2202_06929_b300 as frnn
+from paper_2202_06929_b300 import _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"FRNN_API\s+[\w\s\*]+?\b(frnn_\w+)\s*\(", src))
+    return names
+
+
+def test_header_declares_the_binding_functions():
+    assert declared_functions() == set(_native.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = frnn.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert frnn.version() >= 10000
+
+
+def test_status_strings():
+    for s in range(8):
+        assert frnn.status_string(s)
+    assert frnn.status_string(999) == "unknown status"
+
+
+def test_null_plan_and_bad_params_rejected_on_host():
+    lib = frnn.load()
+    c = _native.frnn_csr()
+    assert lib.frnn_build_graph(None, None, 10, 3, ctypes.c_float(0.1), 4, None, ctypes.byref(c)) == 1
+    off = (ctypes.c_int64 * 2)(0, 10)
+    assert lib.frnn_build_graph_batched(None, None, off, 1, 3, ctypes.c_float(0.1), 4, None, ctypes.byref(c)) == 1
+    assert lib.frnn_get_last_status(None, None) == 1
+    assert lib.frnn_plan_destroy(None) == 0
+    h = ctypes.c_void_p()
+    assert lib.frnn_plan_create(ctypes.byref(h), None) == 1
+    for bad in [dict(d_max=0), dict(d_max=65), dict(k_max_cap=0), dict(k_max_cap=1025),
+                dict(events_max=0), dict(n_max=-1), dict(n_max=1 << 28, k_max_cap=1024)]:
+        kw = dict(device=0, d_max=8, n_max=100, events_max=1, k_max_cap=8)
+        kw.update(bad)
+        prm = _native.frnn_plan_params(**kw)
+        assert lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)) == 1, bad
+
+
+def test_plan_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = frnn.load()
+    h = ctypes.c_void_p()
+    prm = _native.frnn_plan_params(device=0, d_max=8, n_max=100, events_max=1, k_max_cap=8)
+    assert lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)) == frnn.FRNN_ERR_CUDA
+    assert not h.value

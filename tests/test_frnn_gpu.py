@@ -1,0 +1,319 @@
+"""Parity of the CUDA graph build with the CPU oracle, through the C ABI.
+
+Every comparison is exact: row_ptr and col equal element by element (and d2
+bit for bit when emitted).  The CUDA path computes each squared distance with
+the same float32 operations in the same order as the oracle, so the edge sets
+agree on any input, on the 1/256 grid or off it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_06929_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2202_06929_b300 as frnn  # noqa: E402
+
+
+def gpu_csr(x, r, k, emit_d2=False, use_graph=False, tuning=None, plan=None):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, d = x.shape
+    own = plan is None
+    if own:
+        plan = frnn.Plan(n_max=max(n, 1), d_max=d, k_max_cap=max(k, 1), emit_d2=emit_d2,
+                         use_graph=use_graph)
+    try:
+        if tuning:
+            plan.set_tuning(*tuning)
+        xt = torch.from_numpy(x).cuda()
+        csr = plan.build(xt, r, k)
+        host = csr.to_host()
+        st = plan.last_status()
+        return host, st
+    finally:
+        if own:
+            plan.close()
+
+
+def assert_same_as_oracle(x, r, k, **kw):
+    host, st = gpu_csr(x, r, k, emit_d2=True, **kw)
+    assert st == frnn.FRNN_OK, frnn.status_string(st)
+    rp, col, d2 = oracle.radius_graph(x, r, k, with_d2=True)
+    np.testing.assert_array_equal(host["row_ptr"].astype(np.int64), rp)
+    np.testing.assert_array_equal(host["col"], col)
+    np.testing.assert_array_equal(host["d2"].view(np.uint32), d2.view(np.uint32))
+    return host
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_c1_plain_event():
+    x = synth.make_event("c1")
+    assert_same_as_oracle(x, 0.1, 64)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_c1_graph_replay(use_graph):
+    x = synth.make_event("c1")
+    plan = frnn.Plan(n_max=4000, d_max=8, k_max_cap=64, use_graph=use_graph, emit_d2=True)
+    try:
+        rp, col = oracle.radius_graph(x, 0.1, 64)
+        for rep in range(3):  # replays of the same captured graph
+            host, st = gpu_csr(x, 0.1, 64, plan=plan)
+            assert st == 0
+            np.testing.assert_array_equal(host["row_ptr"], rp)
+            np.testing.assert_array_equal(host["col"], col)
+        # a different event through the same plan (and graph)
+        x2 = synth.clustered_grid(3500, 8, 77, 300, 0.03, 0.2)
+        rp2, col2 = oracle.radius_graph(x2, 0.1, 64)
+        host, st = gpu_csr(x2, 0.1, 64, plan=plan)
+        np.testing.assert_array_equal(host["row_ptr"], rp2)
+        np.testing.assert_array_equal(host["col"], col2)
+    finally:
+        plan.close()
+
+
+# ------------------------------------------------------------------ seeded property sweep
+
+SWEEP = []
+_rng = np.random.default_rng(2202)
+for _case in range(28):
+    _d = [1, 2, 3, 5, 8, 12, 16][_case % 7]
+    _k = [1, 2, 31, 32, 33, 64, 256][(_case // 7 + _case) % 7]
+    _n = int(_rng.integers(0, 5001)) if _case % 9 else int(_rng.integers(0, 40))
+    _kind = ["grid", "cluster", "float", "dups"][_case % 4]
+    _r = [0.1, 0.0625, 0.137, 0.25][(_case // 4) % 4]
+    SWEEP.append((_case, _n, _d, _k, _kind, _r))
+
+
+def _make(kind, n, d, seed):
+    if kind == "grid":
+        return synth.uniform_grid(n, d, seed, -64, 64)
+    if kind == "cluster":
+        return synth.clustered_grid(n, d, seed, max(n // 12, 1), 0.04, 0.1)
+    if kind == "float":
+        return synth.uniform_float(n, d, seed, 0.4)
+    return synth.duplicates(n, d, seed, max(n // 20, 1))
+
+
+@pytest.mark.parametrize("case,n,d,k,kind,r", SWEEP, ids=[f"c{c[0]}-n{c[1]}-d{c[2]}-k{c[3]}-{c[4]}" for c in SWEEP])
+def test_property_sweep(case, n, d, k, kind, r):
+    x = _make(kind, n, d, 1000 + case)
+    assert_same_as_oracle(x, r, k)
+
+
+@pytest.mark.parametrize("g_max,scale", [(1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0), (4, 1.5), (3, 2.0), (2, 3.7)])
+def test_tuning_never_changes_result(g_max, scale):
+    x = synth.clustered_grid(4000, 8, 5, 300, 0.03, 0.15)
+    assert_same_as_oracle(x, 0.1, 16, tuning=(g_max, scale))
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_empty_and_single_point():
+    for n in (0, 1):
+        x = np.zeros((n, 5), np.float32)
+        host, st = gpu_csr(x, 0.1, 4, plan=None)
+        assert st == 0
+        assert host["row_ptr"].tolist() == [0] * (n + 1)
+        assert host["col"].size == 0
+
+
+def test_all_identical_points():
+    n, k = 3000, 37
+    x = np.tile(np.array([[0.1, -0.2, 0.3, 0.4, 0.5]], np.float32), (n, 1))
+    host = assert_same_as_oracle(x, 0.01, k)
+    rp, col = host["row_ptr"], host["col"]
+    for i in (0, 1, 36, 37, 2999):
+        assert col[rp[i]:rp[i + 1]].tolist() == [j for j in range(n) if j != i][:k]
+
+
+def test_single_dense_cell_cap_binds():
+    # every point within r of most others: |S_i| >> k, deep top-k selection
+    x = synth.uniform_grid(2500, 3, 9, -6, 6)
+    assert_same_as_oracle(x, 0.05, 100)
+
+
+def test_points_outside_unit_box_and_large_values():
+    rng = np.random.default_rng(4)
+    x = (rng.normal(0, 30.0, size=(3000, 4)) + 1000.0).astype(np.float32)
+    assert_same_as_oracle(x, 3.0, 8)
+
+
+@pytest.mark.parametrize("d", [7, 13, 33, 64])
+def test_dims_not_multiple_of_four_and_wide(d):
+    x = synth.clustered_grid(1500, d, 40 + d, 100, 0.02, 0.1)
+    assert_same_as_oracle(x, 0.05 * np.sqrt(d / 8), 12)
+
+
+@pytest.mark.parametrize("k", [1, 1024])
+def test_extreme_caps(k):
+    x = synth.uniform_grid(3000, 2, 17, -40, 40)
+    assert_same_as_oracle(x, 0.06, k)
+
+
+def test_radius_boundary_inclusive():
+    x = np.array([[0.0, 0.0], [0.125, 0.0], [0.0, 0.12890625]], dtype=np.float32)
+    host = assert_same_as_oracle(x, 0.125, 4)
+    assert host["row_ptr"].tolist() == [0, 1, 2, 2]
+
+
+def test_nonfinite_input_is_reported_and_plan_recovers():
+    x = synth.uniform_grid(500, 4, 3, -20, 20)
+    bad = x.copy()
+    bad[17, 2] = np.nan
+    plan = frnn.Plan(n_max=1000, d_max=4, k_max_cap=8)
+    try:
+        host, st = gpu_csr(bad, 0.1, 8, plan=plan)
+        assert st == frnn.FRNN_ERR_NONFINITE_INPUT
+        assert host["row_ptr"][-1] == 0
+        host, st = gpu_csr(x, 0.1, 8, plan=plan)
+        assert st == 0
+        rp, col = oracle.radius_graph(x, 0.1, 8)
+        np.testing.assert_array_equal(host["col"], col)
+    finally:
+        plan.close()
+
+
+def test_edge_overflow_is_reported_and_plan_recovers():
+    x = synth.clustered_grid(2000, 4, 8, 50, 0.03)
+    rp, col = oracle.radius_graph(x, 0.1, 16)
+    plan = frnn.Plan(n_max=2000, d_max=4, k_max_cap=16, edge_capacity=int(rp[-1]) - 1)
+    try:
+        _, st = gpu_csr(x, 0.1, 16, plan=plan)
+        assert st == frnn.FRNN_ERR_OVERFLOW
+        small = x[:200]
+        rps, cols = oracle.radius_graph(small, 0.1, 16)
+        host, st = gpu_csr(small, 0.1, 16, plan=plan)
+        assert st == 0
+        np.testing.assert_array_equal(host["col"], cols)
+    finally:
+        plan.close()
+
+
+def test_invalid_arguments():
+    plan = frnn.Plan(n_max=100, d_max=4, k_max_cap=8)
+    x = torch.zeros((50, 4), device="cuda")
+    try:
+        for r, k, err in [(0.0, 4, 1), (float("nan"), 4, 1), (-1.0, 4, 1), (0.1, 0, 1), (0.1, 9, 7)]:
+            with pytest.raises(frnn.FrnnError) as ei:
+                plan.build(x, r, k)
+            assert ei.value.status == err
+        with pytest.raises(frnn.FrnnError) as ei:
+            plan.build(torch.zeros((200, 4), device="cuda"), 0.1, 4)
+        assert ei.value.status == frnn.FRNN_ERR_CAPACITY
+        with pytest.raises(frnn.FrnnError) as ei:
+            plan.build(torch.zeros((10, 5), device="cuda"), 0.1, 4)
+        assert ei.value.status == frnn.FRNN_ERR_CAPACITY
+        with pytest.raises(frnn.FrnnError):
+            plan.build_batched(x, [0, 30, 20, 50], 0.1, 4)
+    finally:
+        plan.close()
+
+
+# ------------------------------------------------------------------ batched form
+
+def _events(kind, sizes, d, seed):
+    return [_make(kind, n, d, seed + i) for i, n in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_equals_each_event_alone(use_graph):
+    sizes = [1200, 0, 1, 3500, 777, 2048, 2049, 5]
+    evs = _events("cluster", sizes, 8, 300)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    allx = np.concatenate(evs).astype(np.float32)
+    plan = frnn.Plan(n_max=int(off[-1]), d_max=8, k_max_cap=32, events_max=16, use_graph=use_graph)
+    try:
+        csr = plan.build_batched(torch.from_numpy(allx).cuda(), off, 0.1, 32)
+        host = csr.to_host()
+        assert plan.last_status() == 0
+        for b, x in enumerate(evs):
+            rp, col = csr.event_rows(host, b)
+            orp, ocol = oracle.radius_graph(x, 0.1, 32)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(col, ocol)
+    finally:
+        plan.close()
+
+
+def test_host_to_host_call_matches_device_call():
+    sizes = [900, 1500, 3]
+    evs = _events("grid", sizes, 5, 900)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    allx = np.concatenate(evs).astype(np.float32)
+    plan = frnn.Plan(n_max=int(off[-1]), d_max=5, k_max_cap=16, events_max=4)
+    try:
+        out = plan.build_host(allx, off, 0.09, 16)
+        for b, x in enumerate(evs):
+            lo, hi = off[b], off[b + 1]
+            e0 = out["edge_off"][b]
+            rp = out["row_ptr"][lo:hi + 1].astype(np.int64) - e0
+            col = out["col"][e0:e0 + rp[-1]]
+            orp, ocol = oracle.radius_graph(x, 0.09, 16)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(col, ocol)
+        with pytest.raises(frnn.FrnnError) as ei:
+            plan.build_host(allx, off, 0.09, 16, col_capacity=3)
+        assert ei.value.status == frnn.FRNN_ERR_OVERFLOW
+    finally:
+        plan.close()
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def _sample_queries(n, m, seed):
+    rng = np.random.default_rng(seed)
+    q = rng.choice(n, size=min(m, n), replace=False)
+    return np.unique(np.concatenate([q, [0, n - 1]]))
+
+
+def _check_sampled(x, r, k, host_rp, host_col, queries):
+    orp, ocol = oracle.radius_graph(x, r, k, queries=queries)
+    for qi, i in enumerate(queries):
+        got = host_col[host_rp[i]:host_rp[i + 1]]
+        want = ocol[orp[qi]:orp[qi + 1]]
+        np.testing.assert_array_equal(got, want, err_msg=f"row {i}")
+
+
+def test_c2_full_event_sampled_rows_and_symmetry():
+    """N=120,000, D=8, r=0.1, K=256: sampled rows exact; the cap never binds at
+    this density, so the whole graph must be symmetric."""
+    x = synth.make_event("c2")
+    host, st = gpu_csr(x, 0.1, 256, use_graph=True)
+    assert st == 0
+    rp, col = host["row_ptr"].astype(np.int64), host["col"]
+    _check_sampled(x, 0.1, 256, rp, col, _sample_queries(x.shape[0], 3000, 1))
+    n = x.shape[0]
+    src = np.repeat(np.arange(n), np.diff(rp))
+    a = src.astype(np.int64) * n + col
+    b = col.astype(np.int64) * n + src
+    np.testing.assert_array_equal(np.sort(a), np.sort(b))
+    assert np.all(col != src)
+    # every edge within r: exact grid arithmetic in float64
+    xd = x.astype(np.float64)
+    d2 = ((xd[src] - xd[col]) ** 2).sum(1)
+    assert np.all(d2 * 65536 <= oracle.grid_threshold(0.1))
+
+
+def test_c2_batched_bench_configuration():
+    """The benchmark's configuration: 64 events of N=120,000 (seeded per event),
+    one batched build replayed from a CUDA graph; sampled rows of every event."""
+    n_ev = 64
+    evs = [synth.make_event("c2", e) for e in range(n_ev)]
+    off = np.concatenate([[0], np.cumsum([e.shape[0] for e in evs])]).astype(np.int64)
+    allx = torch.from_numpy(np.concatenate(evs)).cuda()
+    plan = frnn.Plan(n_max=int(off[-1]), d_max=8, k_max_cap=256, events_max=n_ev,
+                     edge_capacity=int(off[-1]) * 64, use_graph=True)
+    try:
+        for rep in range(2):
+            csr = plan.build_batched(allx, off, 0.1, 256)
+            host = csr.to_host()
+            assert plan.last_status() == 0
+        for b in range(0, n_ev, 3):
+            rp, col = csr.event_rows(host, b)
+            _check_sampled(evs[b], 0.1, 256, rp, col, _sample_queries(evs[b].shape[0], 150, b))
+    finally:
+        plan.close()
