@@ -12,7 +12,8 @@ constexpr int kPtThreads = 256;     // threads of the per-point kernels
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kWalkThreads = 256;   // 8 warps, one query per warp at a time
+constexpr int kWalkThreads = 256;   // count walk: 8 warps, 32 queries per warp at a time
+constexpr int kFillThreads = 128;   // fill walk: 4 warps (more shared memory per warp)
 constexpr int kMaxDimCells = 32768; // cells along one hashed dimension (float32 key bound)
 
 // Bits of the device status word (1 << frnn_status).

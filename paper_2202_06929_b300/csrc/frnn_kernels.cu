@@ -536,46 +536,140 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 
 // --------------------------------------------------------------------------
 // Stages 5 and 7: the neighbour-cell walk.
+//
+// Work item: 32 consecutive queries in cell order (a "chunk"), one per lane.
+// The chunk splits into segments of queries that share a cell (and event).
+// For each segment the runs of neighbouring cells are set up once; each lane
+// then holds one candidate of the segment's candidate list at a time and
+// tests it against every query of the segment, two queries per packed f32x2
+// operation.  A candidate is loaded once per segment instead of once per query.
 
 // Squared distance in float32, dims added in order 0, 1, ..., one rounding per
-// operation (no fused multiply-add).  Padding dims are 0 on both sides and add
-// exactly 0, so the value equals the unpadded sequential sum.
+// subtraction, product and addition (no fused multiply-add).  Padding dims are
+// 0 on both sides and add exactly 0, so the value equals the unpadded sum.
+// The f32x2 forms perform the same IEEE single operation on each half.
+__device__ __forceinline__ unsigned long long pk_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// Correctly rounded square of each half.  Written as fma(d, d, +0) rather
+// than mul: ptxas contracts a packed mul.rn followed by add.rn into a packed
+// fma (one rounding instead of two), which changes the sum; an fma whose
+// addend is +0 rounds the product alone and cannot be rewritten as a mul
+// (the two differ for negative-zero products), so the add stays separate.
+__device__ __forceinline__ unsigned long long pk_sqr(unsigned long long d)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(0ull));
+    return r;
+}
+__device__ __forceinline__ unsigned long long pk_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long pk_dup(float c)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(c));
+    return r;
+}
+
+// Candidate coordinates duplicated into both halves of a packed pair.
 template <int DP4>
-__device__ __forceinline__ float dist2(const float4 (&q)[DP4], const float4* row)
+struct CandPk {
+    unsigned long long c[4 * DP4];
+};
+
+template <int DP4>
+__device__ __forceinline__ void load_cand(const float4* row, CandPk<DP4>& cp)
+{
+#pragma unroll
+    for (int k = 0; k < DP4; ++k) {
+        const float4 v = __ldg(row + k);
+        cp.c[4 * k + 0] = pk_dup(v.x);
+        cp.c[4 * k + 1] = pk_dup(v.y);
+        cp.c[4 * k + 2] = pk_dup(v.z);
+        cp.c[4 * k + 3] = pk_dup(v.w);
+    }
+}
+
+// d2 of the query pair stored at qp (dims interleaved: q0[t], q1[t]) against
+// the lane's candidate.  Low half: first query of the pair.
+template <int DP4>
+__device__ __forceinline__ float2 dist2_pair(const ulonglong2* qp, const CandPk<DP4>& cp)
+{
+    unsigned long long s = 0ull;
+#pragma unroll
+    for (int k = 0; k < 2 * DP4; ++k) {
+        const ulonglong2 q = qp[k];  // dims 2k and 2k+1 of both queries
+        unsigned long long d = pk_sub(q.x, cp.c[2 * k]);
+        s = pk_add(s, pk_sqr(d));
+        d = pk_sub(q.y, cp.c[2 * k + 1]);
+        s = pk_add(s, pk_sqr(d));
+    }
+    return make_float2(__uint_as_float((unsigned)s), __uint_as_float((unsigned)(s >> 32)));
+}
+
+// Scalar form for one query (slow path of the fill walk).
+template <int DP4>
+__device__ __forceinline__ float dist2_one(const float* qrow /* smem, interleaved */, int half,
+                                           const float4* crow)
 {
     float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < DP4; ++c) {
-        const float4 v = __ldg(row + c);
+    for (int k = 0; k < DP4; ++k) {
+        const float4 v = __ldg(crow + k);
         float d;
-        d = __fsub_rn(q[c].x, v.x); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(q[c].y, v.y); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(q[c].z, v.z); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(q[c].w, v.w); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(qrow[2 * (4 * k + 0) + half], v.x); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(qrow[2 * (4 * k + 1) + half], v.y); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(qrow[2 * (4 * k + 2) + half], v.z); s = __fadd_rn(s, __fmul_rn(d, d));
+        d = __fsub_rn(qrow[2 * (4 * k + 3) + half], v.w); s = __fadd_rn(s, __fmul_rn(d, d));
     }
     return s;
 }
 
-// Per-warp cache of the current event (a warp's queries mostly stay in one).
-struct WalkEvent {
+// Per-lane cache of the lane's event.
+struct LaneEvent {
     long long lo, hi, pt_off;
-    EvPlan pl;
+    int b;
 };
 
-__device__ __forceinline__ void walk_event(const DevState& st, int n_events, long long q, WalkEvent& we)
+__device__ __forceinline__ void lane_event(const EvDesc* ev, int n_events, long long q, LaneEvent& le)
 {
-    if (q >= we.lo && q < we.hi) return;
-    const int b = event_of_point(st.ev, n_events, q);
-    we.pt_off = st.ev[b].pt_off;
-    we.lo = we.pt_off;
-    we.hi = we.pt_off + st.ev[b].n;
-    we.pl = st.plan[b];
+    if (q >= le.lo && q < le.hi) return;
+    le.b = event_of_point(ev, n_events, q);
+    le.pt_off = ev[le.b].pt_off;
+    le.lo = le.pt_off;
+    le.hi = le.pt_off + ev[le.b].n;
+}
+
+// The fields of an event's plan the walk needs (kept in registers).
+struct SegPlan {
+    int g, skip, cell_off;
+    int ncell[kMaxG], stride[kMaxG];
+};
+
+__device__ __forceinline__ void load_seg_plan(const EvPlan* plan, int b, SegPlan& sp)
+{
+    const EvPlan* p = plan + b;
+    sp.g = p->g;
+    sp.skip = p->skip;
+    sp.cell_off = p->cell_off;
+#pragma unroll
+    for (int t = 0; t < kMaxG; ++t) {
+        sp.ncell[t] = p->ncell[t];
+        sp.stride[t] = p->stride[t];
+    }
 }
 
 // Lane l < 3^(g-1) takes one combination of offsets {-1,0,1} along the g-1
 // slower hashed dims; along the fastest dim the three cells k-1..k+1 are
 // adjacent in memory, so each combination is one contiguous run of points.
-__device__ __forceinline__ void walk_runs(const EvPlan& pl, unsigned cid, const int* cell_start,
+__device__ __forceinline__ void walk_runs(const SegPlan& pl, unsigned cid, const int* cell_start,
                                           int lane, int& beg, int& len)
 {
     int k[kMaxG];
@@ -628,49 +722,124 @@ __device__ __forceinline__ int find_run(int incl, int qi)
     return r;
 }
 
+// Candidate list of one segment: runs prefix-summed across the lanes.
+struct Runs {
+    int beg, incl, excl, total;
+};
+
+__device__ __forceinline__ Runs segment_runs(const SegPlan& pl, unsigned cid, const int* cell_start, int lane)
+{
+    Runs r;
+    int len;
+    walk_runs(pl, cid, cell_start, lane, r.beg, len);
+    r.incl = warp_incl_scan(len, lane);
+    r.excl = r.incl - len;
+    r.total = __shfl_sync(kFull, r.incl, 31);
+    return r;
+}
+
+// Sorted position of candidate number qi of the segment (or -1 past the end).
+__device__ __forceinline__ int candidate_at(const Runs& rn, int qi)
+{
+    const int r = find_run(rn.incl, qi);
+    const int rb = __shfl_sync(kFull, rn.beg, r);
+    const int rx = __shfl_sync(kFull, rn.excl, r);
+    return (qi < rn.total) ? rb + (qi - rx) : -1;
+}
+
+// Load the chunk's queries into shared memory, interleaved by pairs, and find
+// the segments.  Returns the segment-start mask; *nvalid = queries in chunk.
+template <int DP4>
+__device__ __forceinline__ unsigned stage_chunk(const DevState& st, const float4* xs4, long long q, bool valid,
+                                                unsigned cs, int b, float* sq, int lane, int* nvalid)
+{
+    constexpr int DP = 4 * DP4;
+    float* dst = sq + (lane >> 1) * (2 * DP) + (lane & 1);
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < DP4; ++k) {
+            const float4 v = __ldg(xs4 + q * DP4 + k);
+            dst[2 * (4 * k + 0)] = v.x;
+            dst[2 * (4 * k + 1)] = v.y;
+            dst[2 * (4 * k + 2)] = v.z;
+            dst[2 * (4 * k + 3)] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < DP; ++t) dst[2 * t] = 0.f;
+    }
+    __syncwarp();
+    const unsigned up_cs = __shfl_up_sync(kFull, cs, 1);
+    const int up_b = __shfl_up_sync(kFull, b, 1);
+    const bool start = valid && (lane == 0 || cs != up_cs || b != up_b);
+    *nvalid = __popc(__ballot_sync(kFull, valid));
+    return __ballot_sync(kFull, start);
+}
+
 template <int DP4>
 __global__ void __launch_bounds__(kWalkThreads) k_walk_count(DevState st)
 {
+    extern __shared__ float4 s_dyn[];
+    constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
+    float* sq = reinterpret_cast<float*>(s_dyn) + (threadIdx.x >> 5) * (32 * DP);
+    const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
     const int K = st.hdr->k;
     const int B = st.hdr->n_events;
+    const long long nchunks = (P + 31) >> 5;
     const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
-    WalkEvent we;
-    we.lo = 1;
-    we.hi = 0;
-    for (long long q = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); q < P; q += nwarps) {
-        walk_event(st, B, q, we);
+    LaneEvent le;
+    le.lo = 1;
+    le.hi = 0;
+    int plan_b = -1;
+    SegPlan pl;
+    for (long long ch = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); ch < nchunks; ch += nwarps) {
+        const long long q0 = ch << 5;
+        const long long q = q0 + lane;
+        const bool valid = q < P;
+        lane_event(st.ev, B, valid ? q : P - 1, le);
+        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
+        int nvalid;
+        unsigned seg = stage_chunk<DP4>(st, xs4, q, valid, cs, le.b, sq, lane, &nvalid);
         int deg = 0;
-        if (!we.pl.skip) {
-            float4 qv[DP4];
-#pragma unroll
-            for (int c = 0; c < DP4; ++c) qv[c] = __ldg(xs4 + q * DP4 + c);
-            int beg, len;
-            walk_runs(we.pl, __ldg(st.cell_s + q), st.cell_start, lane, beg, len);
-            const int incl = warp_incl_scan(len, lane);
-            const int excl = incl - len;
-            const int T = __shfl_sync(kFull, incl, 31);
-            for (int base = 0; base < T; base += 32) {
-                const int qi = base + lane;
-                const int r = find_run(incl, qi);
-                const int rb = __shfl_sync(kFull, beg, r);
-                const int re = __shfl_sync(kFull, excl, r);
-                bool hit = false;
-                if (qi < T) {
-                    const int cand = rb + (qi - re);
-                    const float d2 = dist2<DP4>(qv, xs4 + (long long)cand * DP4);
-                    hit = (d2 <= r2) && ((long long)cand != q);
+        while (seg) {
+            const int a = __ffs(seg) - 1;
+            seg &= seg - 1;
+            const int e = seg ? __ffs(seg) - 1 : nvalid;
+            const int sb = __shfl_sync(kFull, le.b, a);
+            const unsigned scid = __shfl_sync(kFull, cs, a);
+            if (sb != plan_b) {
+                load_seg_plan(st.plan, sb, pl);
+                plan_b = sb;
+            }
+            if (pl.skip) continue;
+            const Runs rn = segment_runs(pl, scid, st.cell_start, lane);
+            const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
+            for (int base = 0; base < rn.total; base += 32) {
+                const int cand = candidate_at(rn, base + lane);
+                CandPk<DP4> cp;
+                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                const long long cq = (long long)cand - q0;  // candidate's lane if it is in this chunk
+                for (int pp = p0; pp < p1; ++pp) {
+                    const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
+                    const int i0 = 2 * pp, i1 = 2 * pp + 1;
+                    const bool h0 = cand >= 0 && d.x <= r2 && cq != i0 && i0 >= a;
+                    const bool h1 = cand >= 0 && d.y <= r2 && cq != i1 && i1 < e;
+                    const unsigned m0 = __ballot_sync(kFull, h0);
+                    const unsigned m1 = __ballot_sync(kFull, h1);
+                    if (lane == i0) deg += __popc(m0);
+                    if (lane == i1) deg += __popc(m1);
                 }
-                deg += __popc(__ballot_sync(kFull, hit));
             }
         }
-        if (lane == 0) {
+        if (valid) {
             st.deg_s[q] = deg;
-            st.cnt_o[we.pt_off + __ldg(st.perm + q)] = min(deg, K);
+            st.cnt_o[le.pt_off + __ldg(st.perm + q)] = min(deg, K);
         }
+        __syncwarp();
     }
 }
 
@@ -691,7 +860,7 @@ __device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, 
 }
 
 // Ascending bitonic sort of buf[0..n) by one warp (pads to a power of two <= cap).
-__device__ void warp_sort_smem(unsigned long long* buf, int n, int lane)
+__device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, int lane)
 {
     int p2 = 32;
     while (p2 < n) p2 <<= 1;
@@ -714,12 +883,26 @@ __device__ void warp_sort_smem(unsigned long long* buf, int n, int lane)
     }
 }
 
-template <int DP4>
-__global__ void __launch_bounds__(kWalkThreads) k_walk_fill(DevState st, int cap)
+constexpr int kFast = 32;  // rows with |S_i| <= kFast are collected for the whole segment at once
+
+// Keys: (bits(d2) << 32) | j.  d2 >= 0, so the 64-bit order is the (d2, j) order.
+__device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 {
-    extern __shared__ unsigned long long s_keys[];
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+}
+
+template <int DP4>
+__global__ void __launch_bounds__(kFillThreads, 4) k_walk_fill(DevState st, int cap)
+{
+    extern __shared__ float4 s_dyn[];
+    constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
-    unsigned long long* buf = s_keys + (size_t)(threadIdx.x >> 5) * cap;
+    const int wib = threadIdx.x >> 5;
+    const int kreg = cap > 32 * kFast ? cap : 32 * kFast;
+    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (32 * DP);
+    const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (32 * DP)) + (size_t)wib * kreg;
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
@@ -727,73 +910,149 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_fill(DevState st, int cap
     const int B = st.hdr->n_events;
     const int emit = st.hdr->emit_d2;
     const long long ecap = st.hdr->edge_capacity;
-    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const long long nchunks = (P + 31) >> 5;
+    const long long nwarps = (long long)gridDim.x * (kFillThreads / 32);
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
-    WalkEvent we;
-    we.lo = 1;
-    we.hi = 0;
-    for (long long q = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); q < P; q += nwarps) {
-        walk_event(st, B, q, we);
-        if (we.pl.skip) continue;
-        const long long p = we.pt_off + __ldg(st.perm + q);
-        const int rs = st.row_ptr[p];
-        const int re = st.row_ptr[p + 1];
-        const int cnt = re - rs;
-        if (cnt <= 0) continue;
-        if ((long long)re > ecap) continue;  // OVERFLOW was latched by the row scan
-        float4 qv[DP4];
-#pragma unroll
-        for (int c = 0; c < DP4; ++c) qv[c] = __ldg(xs4 + q * DP4 + c);
-        int beg, len;
-        walk_runs(we.pl, __ldg(st.cell_s + q), st.cell_start, lane, beg, len);
-        const int incl = warp_incl_scan(len, lane);
-        const int excl = incl - len;
-        const int T = __shfl_sync(kFull, incl, 31);
-        unsigned long long thr = ~0ull;
-        int nh = 0;
-        for (int base = 0; base < T; base += 32) {
-            const int qi = base + lane;
-            const int r = find_run(incl, qi);
-            const int rb = __shfl_sync(kFull, beg, r);
-            const int rx = __shfl_sync(kFull, excl, r);
-            unsigned long long key = ~0ull;
-            bool take = false;
-            if (qi < T) {
-                const int cand = rb + (qi - rx);
-                const float d2 = dist2<DP4>(qv, xs4 + (long long)cand * DP4);
-                if ((d2 <= r2) && ((long long)cand != q)) {
-                    key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__ldg(st.perm + cand);
-                    take = key < thr;
-                }
-            }
-            unsigned m = __ballot_sync(kFull, take);
-            if (m == 0u) continue;
-            if (nh + 32 > cap) {
-                // only reached when |S_i| > k: keep the k smallest so far
-                warp_sort_smem(buf, nh, lane);
-                nh = K;
-                thr = buf[K - 1];
-                take = take && (key < thr);
-                m = __ballot_sync(kFull, take);
-            }
-            if (take) buf[nh + __popc(m & lt_mask)] = key;
-            nh += __popc(m);
-            __syncwarp();
+    LaneEvent le;
+    le.lo = 1;
+    le.hi = 0;
+    int plan_b = -1;
+    SegPlan pl;
+    for (long long ch = (long long)blockIdx.x * (kFillThreads / 32) + wib; ch < nchunks; ch += nwarps) {
+        const long long q0 = ch << 5;
+        const long long q = q0 + lane;
+        const bool valid = q < P;
+        lane_event(st.ev, B, valid ? q : P - 1, le);
+        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
+        int rs = 0, cnt = 0, dg = 0;
+        if (valid) {
+            const long long p = le.pt_off + __ldg(st.perm + q);
+            rs = st.row_ptr[p];
+            const int re = st.row_ptr[p + 1];
+            cnt = ((long long)re <= ecap) ? re - rs : 0;  // over capacity: OVERFLOW already latched
+            dg = st.deg_s[q];
         }
-        const int nout = min(cnt, nh);
-        if (nh <= 32) {
-            unsigned long long v = (lane < nh) ? buf[lane] : ~0ull;
-            v = warp_sort32(v, lane);
-            if (lane < nout) {
-                st.col[rs + lane] = (int)(unsigned)v;
-                if (emit) st.d2[rs + lane] = __uint_as_float((unsigned)(v >> 32));
+        int nvalid;
+        unsigned seg = stage_chunk<DP4>(st, xs4, q, valid, cs, le.b, sq, lane, &nvalid);
+        const unsigned fast_all = __ballot_sync(kFull, cnt > 0 && dg <= kFast);
+        const unsigned slow_all = __ballot_sync(kFull, cnt > 0 && dg > kFast);
+        int nh = 0;  // keys collected for this lane's query (fast path)
+        while (seg) {
+            const int a = __ffs(seg) - 1;
+            seg &= seg - 1;
+            const int e = seg ? __ffs(seg) - 1 : nvalid;
+            const unsigned smask = (e >= 32 ? kFull : ((1u << e) - 1u)) & ~((1u << a) - 1u);
+            const unsigned fmask = fast_all & smask;
+            unsigned wmask = slow_all & smask;
+            if (!(fmask | wmask)) continue;
+            const int sb = __shfl_sync(kFull, le.b, a);
+            const unsigned scid = __shfl_sync(kFull, cs, a);
+            if (sb != plan_b) {
+                load_seg_plan(st.plan, sb, pl);
+                plan_b = sb;
             }
-        } else {
-            warp_sort_smem(buf, nh, lane);
-            for (int e2 = lane; e2 < nout; e2 += 32) {
-                const unsigned long long v = buf[e2];
-                st.col[rs + e2] = (int)(unsigned)v;
-                if (emit) st.d2[rs + e2] = __uint_as_float((unsigned)(v >> 32));
+            if (pl.skip) continue;
+            const Runs rn = segment_runs(pl, scid, st.cell_start, lane);
+            if (fmask) {
+                // pairs that hold at least one fast query
+                const int pa = (__ffs(fmask) - 1) >> 1, pz = (31 - __clz(fmask)) >> 1;
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    CandPk<DP4> cp;
+                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                    const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
+                    const long long cq = (long long)cand - q0;
+                    for (int pp = pa; pp <= pz; ++pp) {
+                        const int i0 = 2 * pp, i1 = 2 * pp + 1;
+                        const bool f0 = (fmask >> i0) & 1u, f1 = (fmask >> i1) & 1u;
+                        if (!(f0 | f1)) continue;
+                        const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
+                        const bool h0 = f0 && cand >= 0 && d.x <= r2 && cq != i0;
+                        const bool h1 = f1 && cand >= 0 && d.y <= r2 && cq != i1;
+                        const unsigned m0 = __ballot_sync(kFull, h0);
+                        const unsigned m1 = __ballot_sync(kFull, h1);
+                        const int b0 = __shfl_sync(kFull, nh, i0);
+                        const int b1 = __shfl_sync(kFull, nh, i1);
+                        if (h0) keys[i0 * kFast + b0 + __popc(m0 & lt_mask)] = edge_key(d.x, j);
+                        if (h1) keys[i1 * kFast + b1 + __popc(m1 & lt_mask)] = edge_key(d.y, j);
+                        if (lane == i0) nh += __popc(m0);
+                        if (lane == i1) nh += __popc(m1);
+                    }
+                }
+                __syncwarp();
+                // each collected row: rank of every key among the row's keys
+                unsigned fm = fmask;
+                while (fm) {
+                    const int i = __ffs(fm) - 1;
+                    fm &= fm - 1;
+                    const int n = __shfl_sync(kFull, nh, i);
+                    const int rsi = __shfl_sync(kFull, rs, i);
+                    const int cnti = __shfl_sync(kFull, cnt, i);
+                    const unsigned long long* row = keys + i * kFast;
+                    if (lane < n) {
+                        const unsigned long long kk = row[lane];
+                        int rank = 0;
+                        for (int m = 0; m < n; ++m) rank += row[m] < kk;
+                        if (rank < cnti) {
+                            st.col[rsi + rank] = (int)(unsigned)kk;
+                            if (emit) st.d2[rsi + rank] = __uint_as_float((unsigned)(kk >> 32));
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // rows with |S_i| > kFast, one at a time: keep the k smallest keys
+            while (wmask) {
+                const int i = __ffs(wmask) - 1;
+                wmask &= wmask - 1;
+                const int rsi = __shfl_sync(kFull, rs, i);
+                const int cnti = __shfl_sync(kFull, cnt, i);
+                const float* qrow = sq + (i >> 1) * (2 * DP);
+                const int half = i & 1;
+                unsigned long long thr = ~0ull;
+                int nk = 0;
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    unsigned long long key = ~0ull;
+                    bool take = false;
+                    if (cand >= 0) {
+                        const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
+                        if (d2 <= r2 && (long long)cand != q0 + i) {
+                            key = edge_key(d2, __ldg(st.perm + cand));
+                            take = key < thr;
+                        }
+                    }
+                    unsigned m = __ballot_sync(kFull, take);
+                    if (m == 0u) continue;
+                    if (nk + 32 > cap) {
+                        // only reached when |S_i| > k: keep the k smallest so far
+                        warp_sort_smem(keys, nk, lane);
+                        nk = K;
+                        thr = keys[K - 1];
+                        take = take && (key < thr);
+                        m = __ballot_sync(kFull, take);
+                    }
+                    if (take) keys[nk + __popc(m & lt_mask)] = key;
+                    nk += __popc(m);
+                    __syncwarp();
+                }
+                const int nout = min(cnti, nk);
+                if (nk <= 32) {
+                    unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
+                    v = warp_sort32(v, lane);
+                    if (lane < nout) {
+                        st.col[rsi + lane] = (int)(unsigned)v;
+                        if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
+                    }
+                } else {
+                    warp_sort_smem(keys, nk, lane);
+                    for (int e2 = lane; e2 < nout; e2 += 32) {
+                        const unsigned long long v = keys[e2];
+                        st.col[rsi + e2] = (int)(unsigned)v;
+                        if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
+                    }
+                }
+                __syncwarp();
             }
         }
         __syncwarp();
@@ -808,14 +1067,24 @@ inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
 }
 
 template <int DP4>
+int count_smem() { return (kWalkThreads / 32) * 32 * 4 * DP4 * (int)sizeof(float); }
+
+template <int DP4>
+int fill_smem(int cap)
+{
+    const int kreg = cap > 32 * kFast ? cap : 32 * kFast;
+    return (kFillThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + kreg * (int)sizeof(unsigned long long));
+}
+
+template <int DP4>
 cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t s, cudaEvent_t* ev)
 {
     mark(ev, 4, s);
-    k_walk_count<DP4><<<cfg.grid_count, kWalkThreads, 0, s>>>(st);
+    k_walk_count<DP4><<<cfg.grid_count, kWalkThreads, count_smem<DP4>(), s>>>(st);
     mark(ev, 5, s);
     k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 6, s);
-    k_walk_fill<DP4><<<cfg.grid_fill, kWalkThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
+    k_walk_fill<DP4><<<cfg.grid_fill, kFillThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
     mark(ev, 7, s);
     return cudaGetLastError();
 }
@@ -823,18 +1092,21 @@ cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t 
 template <int DP4>
 cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
 {
-    const int smem = (kWalkThreads / 32) * fill_cap * (int)sizeof(unsigned long long);
-    cudaError_t e = cudaFuncSetAttribute(k_walk_fill<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int csm = count_smem<DP4>();
+    const int fsm = fill_smem<DP4>(fill_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_count<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_walk_fill<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e != cudaSuccess) return e;
     int nb_c = 0, nb_f = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_count<DP4>, kWalkThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_count<DP4>, kWalkThreads, csm);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_fill<DP4>, kWalkThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_fill<DP4>, kFillThreads, fsm);
     if (e != cudaSuccess) return e;
     cfg->grid_count = n_sm * (nb_c > 0 ? nb_c : 1);
     cfg->grid_fill = n_sm * (nb_f > 0 ? nb_f : 1);
     cfg->fill_cap = fill_cap;
-    cfg->fill_smem = smem;
+    cfg->fill_smem = fsm;
     return cudaSuccess;
 }
 
