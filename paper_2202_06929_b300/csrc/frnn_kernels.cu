@@ -647,10 +647,15 @@ __device__ __forceinline__ void lane_event(const EvDesc* ev, int n_events, long 
     le.hi = le.pt_off + ev[le.b].n;
 }
 
-// The fields of an event's plan the walk needs (kept in registers).
+// The fields of an event's plan the walk needs, as scalars so that they stay
+// in registers (an indexed array here ended up in local memory).
 struct SegPlan {
     int g, skip, cell_off;
-    int ncell[kMaxG], stride[kMaxG];
+    int nc0, nc1, nc2, nc3;
+    int st0, st1, st2;       // strides of the slower dims (the fastest has stride 1)
+    int dm0, dm1, dm2, dm3;  // hashed embedding dims
+    float lo0, lo1, lo2, lo3;
+    float inv_s;
 };
 
 __device__ __forceinline__ void load_seg_plan(const EvPlan* plan, int b, SegPlan& sp)
@@ -659,50 +664,58 @@ __device__ __forceinline__ void load_seg_plan(const EvPlan* plan, int b, SegPlan
     sp.g = p->g;
     sp.skip = p->skip;
     sp.cell_off = p->cell_off;
-#pragma unroll
-    for (int t = 0; t < kMaxG; ++t) {
-        sp.ncell[t] = p->ncell[t];
-        sp.stride[t] = p->stride[t];
-    }
+    sp.nc0 = p->ncell[0]; sp.nc1 = p->ncell[1]; sp.nc2 = p->ncell[2]; sp.nc3 = p->ncell[3];
+    sp.st0 = p->stride[0]; sp.st1 = p->stride[1]; sp.st2 = p->stride[2];
+    sp.dm0 = p->dims[0]; sp.dm1 = p->dims[1]; sp.dm2 = p->dims[2]; sp.dm3 = p->dims[3];
+    sp.lo0 = p->lo[0]; sp.lo1 = p->lo[1]; sp.lo2 = p->lo[2]; sp.lo3 = p->lo[3];
+    sp.inv_s = p->inv_s;
 }
 
-// Lane l < 3^(g-1) takes one combination of offsets {-1,0,1} along the g-1
-// slower hashed dims; along the fastest dim the three cells k-1..k+1 are
-// adjacent in memory, so each combination is one contiguous run of points.
-__device__ __forceinline__ void walk_runs(const SegPlan& pl, unsigned cid, const int* cell_start,
-                                          int lane, int& beg, int& len)
+// Runs of the segment whose first query is staged at qrow[2 t + half].  Its
+// cell coordinates are recomputed from its coordinates with the operations
+// of cell_coord(), so they equal those the key kernel used.  Lane l < 3^(g-1)
+// takes one combination of offsets {-1,0,1} along the g-1 slower hashed dims;
+// along the fastest dim the three cells k-1..k+1 are adjacent in memory, so
+// each combination is one contiguous run of points.
+__device__ __forceinline__ void walk_runs(const SegPlan& pl, const float* qrow, int half,
+                                          const int* cell_start, int lane, int& beg, int& len)
 {
-    int k[kMaxG];
-#pragma unroll
-    for (int t = 0; t < kMaxG; ++t) k[t] = (t < pl.g) ? (int)((cid / (unsigned)pl.stride[t]) % (unsigned)pl.ncell[t]) : 0;
-    int nr = 1;
-#pragma unroll
-    for (int t = 0; t < kMaxG - 1; ++t) if (t < pl.g - 1) nr *= 3;
+    const int g = pl.g;
+    const int k0 = cell_coord(qrow[2 * pl.dm0 + half], pl.lo0, pl.inv_s, pl.nc0);
+    const int k1 = g > 1 ? cell_coord(qrow[2 * pl.dm1 + half], pl.lo1, pl.inv_s, pl.nc1) : 0;
+    const int k2 = g > 2 ? cell_coord(qrow[2 * pl.dm2 + half], pl.lo2, pl.inv_s, pl.nc2) : 0;
+    const int k3 = g > 3 ? cell_coord(qrow[2 * pl.dm3 + half], pl.lo3, pl.inv_s, pl.nc3) : 0;
+    const int nr = g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
     beg = 0;
     len = 0;
     if (lane < nr) {
-        int rem = lane, cbase = 0;
+        const int o0 = lane % 3 - 1, o1 = (lane / 3) % 3 - 1, o2 = (lane / 9) % 3 - 1;
         bool ok = true;
-#pragma unroll
-        for (int t = 0; t < kMaxG - 1; ++t) {
-            if (t < pl.g - 1) {
-                const int kt = k[t] + (rem % 3) - 1;
-                rem /= 3;
-                ok &= (kt >= 0) && (kt < pl.ncell[t]);
-                cbase += kt * pl.stride[t];
-            }
+        int cb = 0, kl = k0, ncl = pl.nc0;
+        if (g > 1) {
+            const int kt = k0 + o0;
+            ok &= (kt >= 0) && (kt < pl.nc0);
+            cb += kt * pl.st0;
+            kl = k1;
+            ncl = pl.nc1;
+        }
+        if (g > 2) {
+            const int kt = k1 + o1;
+            ok &= (kt >= 0) && (kt < pl.nc1);
+            cb += kt * pl.st1;
+            kl = k2;
+            ncl = pl.nc2;
+        }
+        if (g > 3) {
+            const int kt = k2 + o2;
+            ok &= (kt >= 0) && (kt < pl.nc2);
+            cb += kt * pl.st2;
+            kl = k3;
+            ncl = pl.nc3;
         }
         if (ok) {
-            int kl = 0, ncl = 1;
-#pragma unroll
-            for (int t = 0; t < kMaxG; ++t) {
-                if (t == pl.g - 1) {
-                    kl = k[t];
-                    ncl = pl.ncell[t];
-                }
-            }
-            const int c0 = cbase + max(kl - 1, 0);
-            const int c1 = cbase + min(kl + 1, ncl - 1);
+            const int c0 = cb + max(kl - 1, 0);
+            const int c1 = cb + min(kl + 1, ncl - 1);
             beg = cell_start[pl.cell_off + c0];
             len = cell_start[pl.cell_off + c1 + 1] - beg;
         }
@@ -727,11 +740,12 @@ struct Runs {
     int beg, incl, excl, total;
 };
 
-__device__ __forceinline__ Runs segment_runs(const SegPlan& pl, unsigned cid, const int* cell_start, int lane)
+__device__ __forceinline__ Runs segment_runs(const SegPlan& pl, const float* qrow, int half,
+                                             const int* cell_start, int lane)
 {
     Runs r;
     int len;
-    walk_runs(pl, cid, cell_start, lane, r.beg, len);
+    walk_runs(pl, qrow, half, cell_start, lane, r.beg, len);
     r.incl = warp_incl_scan(len, lane);
     r.excl = r.incl - len;
     r.total = __shfl_sync(kFull, r.incl, 31);
@@ -777,7 +791,7 @@ __device__ __forceinline__ unsigned stage_chunk(const DevState& st, const float4
 }
 
 template <int DP4>
-__global__ void __launch_bounds__(kWalkThreads) k_walk_count(DevState st)
+__global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_count(DevState st)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
@@ -810,19 +824,19 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk_count(DevState st)
             seg &= seg - 1;
             const int e = seg ? __ffs(seg) - 1 : nvalid;
             const int sb = __shfl_sync(kFull, le.b, a);
-            const unsigned scid = __shfl_sync(kFull, cs, a);
             if (sb != plan_b) {
                 load_seg_plan(st.plan, sb, pl);
                 plan_b = sb;
             }
             if (pl.skip) continue;
-            const Runs rn = segment_runs(pl, scid, st.cell_start, lane);
+            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
             const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
                 CandPk<DP4> cp;
                 load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
                 const long long cq = (long long)cand - q0;  // candidate's lane if it is in this chunk
+#pragma unroll 2
                 for (int pp = p0; pp < p1; ++pp) {
                     const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
                     const int i0 = 2 * pp, i1 = 2 * pp + 1;
@@ -892,7 +906,7 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 }
 
 template <int DP4>
-__global__ void __launch_bounds__(kFillThreads, 4) k_walk_fill(DevState st, int cap)
+__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_fill(DevState st, int cap)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
@@ -946,13 +960,12 @@ __global__ void __launch_bounds__(kFillThreads, 4) k_walk_fill(DevState st, int 
             unsigned wmask = slow_all & smask;
             if (!(fmask | wmask)) continue;
             const int sb = __shfl_sync(kFull, le.b, a);
-            const unsigned scid = __shfl_sync(kFull, cs, a);
             if (sb != plan_b) {
                 load_seg_plan(st.plan, sb, pl);
                 plan_b = sb;
             }
             if (pl.skip) continue;
-            const Runs rn = segment_runs(pl, scid, st.cell_start, lane);
+            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
             if (fmask) {
                 // pairs that hold at least one fast query
                 const int pa = (__ffs(fmask) - 1) >> 1, pz = (31 - __clz(fmask)) >> 1;
