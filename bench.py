@@ -44,7 +44,7 @@ METRIC = "FRNN graph-build events/s at N=120k,D=8 batched vs plain; p50/p99 late
 UNIT = "events/s"
 N_PER_EVENT, D, R, K = 120_000, 8, 0.1, 256
 KERNELS_PER_BUILD = 7
-STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_count", "scan_rows", "walk_fill")
+STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -195,9 +195,11 @@ def stage_bytes(n_total: int, n_edges: int, d: int):
         "key_hist": 4 * n_total * d + 8 * n_total,
         "scan_cells": 0,  # size of the cell table, reported separately
         "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total,
-        "walk_count": 4 * n_total * dp + 8 * n_total,
+        # sorted points read once; per point its cell id, count and pool slot; rows parked
+        "walk_collect": 4 * n_total * dp + 4 * n_total + 8 * n_total + 4 * n_edges,
         "scan_rows": 8 * n_total,
-        "walk_fill": 4 * n_total * dp + 4 * (n_total + 1) + 4 * n_edges + 4 * n_total,
+        # per point perm, pool slot and row_ptr; rows read from the pool and written to col
+        "walk_emit": 8 * n_total + 4 * (n_total + 1) + 8 * n_edges,
     }
 
 
@@ -389,7 +391,7 @@ def main(argv=None):
                       "note": "one event per call (CUDA graph replay per event), device time per event"},
             "batched_over_plain": value / plain_value / world,
             "stages_ms": stage_avg,
-            "roofline": {"bound": "hbm", "kernel": f"k_walk_{dom.split('_')[-1]}" if dom.startswith("walk") else dom,
+            "roofline": {"bound": "hbm", "kernel": "k_" + dom,
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": sbytes[dom],

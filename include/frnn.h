@@ -168,7 +168,7 @@ FRNN_API int frnn_build_graph_host(frnn_plan* plan, const float* h_emb, const in
  * for profiling.  Never replays a CUDA graph.  Synchronous: waits for the
  * build, then writes the device time of each stage in milliseconds to
  * stage_ms[0..6]: bounding box and cell grid, cell ids and histogram, cell
- * scan, scatter into cell order, count walk, row scan, fill walk.
+ * scan, scatter into cell order, collect walk, row scan, emit walk.
  * n_stages must be >= 7.  Errors: as frnn_build_graph_batched.
  */
 FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const int64_t* ev_off,

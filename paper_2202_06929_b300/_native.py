@@ -264,7 +264,7 @@ class Plan:
                                                ctypes.byref(c)), "frnn_build_graph_batched")
         return Csr(c, self.device, off, self.edge_capacity)
 
-    STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_count", "scan_rows", "walk_fill")
+    STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
 
     def build_profiled(self, emb, ev_off, r: float, k: int, stream=None):
         """Batched build with CUDA events between the stages (synchronous).

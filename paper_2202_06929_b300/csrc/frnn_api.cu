@@ -122,6 +122,7 @@ int reset_device_state(frnn_plan* p, cudaStream_t s)
     ok &= cudaMemsetAsync(st.chunk_done, 0, sizeof(unsigned) * ev, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.nonfinite, 0, sizeof(unsigned) * ev, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.counters, 0, sizeof(unsigned) * kCtrCount, s) == cudaSuccess;
+    ok &= cudaMemsetAsync(st.pool_ctr, 0, sizeof(unsigned long long), s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.cell_count, 0, sizeof(unsigned) * p->cells_max, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.scan_cells, 0, sizeof(unsigned long long) * p->tiles_cells, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.scan_rows, 0, sizeof(unsigned long long) * p->tiles_rows, s) == cudaSuccess;
@@ -341,7 +342,7 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.perm, n);
     ALLOC(st.cell_s, n);
     ALLOC(st.xs, n * p->dp_max);
-    ALLOC(st.deg_s, n);
+    ALLOC(st.pool_off, n);
     ALLOC(st.cnt_o, n);
     ALLOC(st.row_ptr, n + 1);
     ALLOC(st.cell_count, cells_max);
@@ -350,6 +351,9 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.scan_rows, (long long)p->tiles_rows);
     ALLOC(st.col, q.edge_capacity);
     if (q.flags & FRNN_EMIT_D2) ALLOC(st.d2, q.edge_capacity);
+    ALLOC(st.pool, q.edge_capacity);
+    if (q.flags & FRNN_EMIT_D2) ALLOC(st.pool_d2, q.edge_capacity);
+    ALLOC(st.pool_ctr, 1);
     ALLOC(st.edge_off, ev + 1);
     ALLOC(st.status, 1);
 #undef ALLOC

@@ -83,7 +83,7 @@ struct DevState {
     int* perm;               // [n_max] sorted position -> event-local point index
     unsigned* cell_s;        // [n_max] sorted position -> cell id
     float* xs;               // [n_max * dp_max] points in cell order, rows padded with 0
-    int* deg_s;              // [n_max] sorted position -> |S_i|
+    int* pool_off;           // [n_max] sorted position -> first pool slot of its row, or -1
     int* cnt_o;              // [n_max] point -> min(|S_i|, k)
     int* row_ptr;            // [n_max + 1]
     unsigned* cell_count;    // [cells_max], zero between builds
@@ -92,6 +92,9 @@ struct DevState {
     unsigned long long* scan_rows;
     int* col;
     float* d2;
+    int* pool;               // [edge_capacity] short rows, sorted, parked by the collect walk
+    float* pool_d2;          // [edge_capacity] their d2 (FRNN_EMIT_D2 only)
+    unsigned long long* pool_ctr;  // next free pool slot; zero between builds
     int* edge_off;           // [events_max + 1]
     unsigned* status;
 };

@@ -15,11 +15,13 @@
 //                   which also clears the histogram for the next build
 //   4 k_scatter     points copied into cell order, rows padded to a multiple
 //                   of four floats for 16-byte loads
-//   5 k_walk_count  one warp per query: walk the 3^(g-1) runs of neighbouring
-//                   cells, count the points within r (the degree |S_i|)
+//   5 k_walk_collect  a warp takes 32 queries in cell order; per cell it walks
+//                   the 3^(g-1) runs of neighbouring cells and counts the points
+//                   within r (|S_i|); rows of at most 32 neighbours are sorted
+//                   by (d2, j), cut at k and parked in a pool
 //   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr
-//   7 k_walk_fill   the same walk again, keeping the k smallest (d2, j) keys,
-//                   written to col in increasing order
+//   7 k_walk_emit   pooled rows copied into CSR order; longer rows walked again,
+//                   keeping the k smallest (d2, j) keys
 //
 // Paper: Sec. 3.4 (fixed-radius neighbours by a grid of cells, cost growing
 // as 3^g with the gridded dimensions g, which is why at most four are used)
@@ -483,7 +485,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
     }
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
     if (MODE == 1) {
-        // per-event edge offsets, and the capacity check of the fill walk
+        if (threadIdx.x == 0) *st.pool_ctr = 0ull;  // the collect walk is done with it
+        // per-event edge offsets, and the capacity check of the emit walk
         const int B = st.hdr->n_events;
         for (int b = threadIdx.x; b <= B; b += blockDim.x) {
             const long long p = (b < B) ? st.ev[b].pt_off : M;
@@ -761,11 +764,10 @@ __device__ __forceinline__ int candidate_at(const Runs& rn, int qi)
     return (qi < rn.total) ? rb + (qi - rx) : -1;
 }
 
-// Load the chunk's queries into shared memory, interleaved by pairs, and find
-// the segments.  Returns the segment-start mask; *nvalid = queries in chunk.
+// Load the chunk's queries into shared memory, interleaved by pairs: query i
+// sits at sq[(i / 2) * 2 DP + 2 t + (i % 2)] for dim t.
 template <int DP4>
-__device__ __forceinline__ unsigned stage_chunk(const DevState& st, const float4* xs4, long long q, bool valid,
-                                                unsigned cs, int b, float* sq, int lane, int* nvalid)
+__device__ __forceinline__ void stage_queries(const float4* xs4, long long q, bool valid, float* sq, int lane)
 {
     constexpr int DP = 4 * DP4;
     float* dst = sq + (lane >> 1) * (2 * DP) + (lane & 1);
@@ -783,78 +785,20 @@ __device__ __forceinline__ unsigned stage_chunk(const DevState& st, const float4
         for (int t = 0; t < DP; ++t) dst[2 * t] = 0.f;
     }
     __syncwarp();
+}
+
+// Stage the chunk and find its segments (runs of lanes with the same cell
+// and event).  Returns the segment-start mask; *nvalid = queries in chunk.
+template <int DP4>
+__device__ __forceinline__ unsigned stage_chunk(const float4* xs4, long long q, bool valid, unsigned cs, int b,
+                                                float* sq, int lane, int* nvalid)
+{
+    stage_queries<DP4>(xs4, q, valid, sq, lane);
     const unsigned up_cs = __shfl_up_sync(kFull, cs, 1);
     const int up_b = __shfl_up_sync(kFull, b, 1);
     const bool start = valid && (lane == 0 || cs != up_cs || b != up_b);
     *nvalid = __popc(__ballot_sync(kFull, valid));
     return __ballot_sync(kFull, start);
-}
-
-template <int DP4>
-__global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_count(DevState st)
-{
-    extern __shared__ float4 s_dyn[];
-    constexpr int DP = 4 * DP4;
-    const int lane = threadIdx.x & 31;
-    float* sq = reinterpret_cast<float*>(s_dyn) + (threadIdx.x >> 5) * (32 * DP);
-    const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
-    const long long P = st.hdr->n_total;
-    const float r2 = st.hdr->r2;
-    const int K = st.hdr->k;
-    const int B = st.hdr->n_events;
-    const long long nchunks = (P + 31) >> 5;
-    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
-    const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
-    LaneEvent le;
-    le.lo = 1;
-    le.hi = 0;
-    int plan_b = -1;
-    SegPlan pl;
-    for (long long ch = (long long)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5); ch < nchunks; ch += nwarps) {
-        const long long q0 = ch << 5;
-        const long long q = q0 + lane;
-        const bool valid = q < P;
-        lane_event(st.ev, B, valid ? q : P - 1, le);
-        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
-        int nvalid;
-        unsigned seg = stage_chunk<DP4>(st, xs4, q, valid, cs, le.b, sq, lane, &nvalid);
-        int deg = 0;
-        while (seg) {
-            const int a = __ffs(seg) - 1;
-            seg &= seg - 1;
-            const int e = seg ? __ffs(seg) - 1 : nvalid;
-            const int sb = __shfl_sync(kFull, le.b, a);
-            if (sb != plan_b) {
-                load_seg_plan(st.plan, sb, pl);
-                plan_b = sb;
-            }
-            if (pl.skip) continue;
-            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
-            const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
-            for (int base = 0; base < rn.total; base += 32) {
-                const int cand = candidate_at(rn, base + lane);
-                CandPk<DP4> cp;
-                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                const long long cq = (long long)cand - q0;  // candidate's lane if it is in this chunk
-#pragma unroll 2
-                for (int pp = p0; pp < p1; ++pp) {
-                    const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
-                    const int i0 = 2 * pp, i1 = 2 * pp + 1;
-                    const bool h0 = cand >= 0 && d.x <= r2 && cq != i0 && i0 >= a;
-                    const bool h1 = cand >= 0 && d.y <= r2 && cq != i1 && i1 < e;
-                    const unsigned m0 = __ballot_sync(kFull, h0);
-                    const unsigned m1 = __ballot_sync(kFull, h1);
-                    if (lane == i0) deg += __popc(m0);
-                    if (lane == i1) deg += __popc(m1);
-                }
-            }
-        }
-        if (valid) {
-            st.deg_s[q] = deg;
-            st.cnt_o[le.pt_off + __ldg(st.perm + q)] = min(deg, K);
-        }
-        __syncwarp();
-    }
 }
 
 // Warp-wide ascending bitonic sort of one 64-bit key per lane.
@@ -897,7 +841,10 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
     }
 }
 
-constexpr int kFast = 32;  // rows with |S_i| <= kFast are collected for the whole segment at once
+// Rows with |S_i| <= kFast are kept whole by the collect walk (one 32-key
+// slot per query in shared memory) and sorted there; longer rows are left to
+// the emit walk, which selects the k smallest keys on its own.
+constexpr int kFast = 32;
 
 // Keys: (bits(d2) << 32) | j.  d2 >= 0, so the 64-bit order is the (d2, j) order.
 __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
@@ -905,18 +852,131 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
     return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
 }
 
+// Stage 5: count every query's neighbours; rows of at most kFast neighbours
+// are also collected, sorted, cut at k and written to the pool (space taken
+// per chunk from a counter), so that stage 7 only copies them.
 template <int DP4>
-__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_fill(DevState st, int cap)
+__global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect(DevState st)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int kreg = cap > 32 * kFast ? cap : 32 * kFast;
     float* sq = reinterpret_cast<float*>(s_dyn) + wib * (32 * DP);
     const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(
-        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (32 * DP)) + (size_t)wib * kreg;
+        reinterpret_cast<float*>(s_dyn) + (kWalkThreads / 32) * (32 * DP)) + (size_t)wib * (32 * kFast);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long P = st.hdr->n_total;
+    const float r2 = st.hdr->r2;
+    const int K = st.hdr->k;
+    const int B = st.hdr->n_events;
+    const int emit = st.hdr->emit_d2;
+    const long long pool_cap = st.hdr->edge_capacity;
+    const long long nchunks = (P + 31) >> 5;
+    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
+    LaneEvent le;
+    le.lo = 1;
+    le.hi = 0;
+    int plan_b = -1;
+    SegPlan pl;
+    for (long long ch = (long long)blockIdx.x * (kWalkThreads / 32) + wib; ch < nchunks; ch += nwarps) {
+        const long long q0 = ch << 5;
+        const long long q = q0 + lane;
+        const bool valid = q < P;
+        lane_event(st.ev, B, valid ? q : P - 1, le);
+        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
+        int nvalid;
+        unsigned seg = stage_chunk<DP4>(xs4, q, valid, cs, le.b, sq, lane, &nvalid);
+        int deg = 0;
+        while (seg) {
+            const int a = __ffs(seg) - 1;
+            seg &= seg - 1;
+            const int e = seg ? __ffs(seg) - 1 : nvalid;
+            const int sb = __shfl_sync(kFull, le.b, a);
+            if (sb != plan_b) {
+                load_seg_plan(st.plan, sb, pl);
+                plan_b = sb;
+            }
+            if (pl.skip) continue;
+            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
+            const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
+            for (int base = 0; base < rn.total; base += 32) {
+                const int cand = candidate_at(rn, base + lane);
+                CandPk<DP4> cp;
+                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
+                const long long cq = (long long)cand - q0;  // candidate's lane if it is in this chunk
+#pragma unroll 2
+                for (int pp = p0; pp < p1; ++pp) {
+                    const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
+                    const int i0 = 2 * pp, i1 = 2 * pp + 1;
+                    const bool h0 = cand >= 0 && d.x <= r2 && cq != i0 && i0 >= a;
+                    const bool h1 = cand >= 0 && d.y <= r2 && cq != i1 && i1 < e;
+                    const unsigned m0 = __ballot_sync(kFull, h0);
+                    const unsigned m1 = __ballot_sync(kFull, h1);
+                    const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
+                    const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
+                    if (h0 && s0 < kFast) keys[i0 * kFast + s0] = edge_key(d.x, j);
+                    if (h1 && s1 < kFast) keys[i1 * kFast + s1] = edge_key(d.y, j);
+                    if (lane == i0) deg += __popc(m0);
+                    if (lane == i1) deg += __popc(m1);
+                }
+            }
+        }
+        // pool space for the chunk's short rows
+        const int cnt = min(deg, K);
+        const bool fast = valid && deg > 0 && deg <= kFast;
+        const int need = fast ? cnt : 0;
+        const int incl = warp_incl_scan(need, lane);
+        const int tot = __shfl_sync(kFull, incl, 31);
+        unsigned long long base_off = 0ull;
+        if (lane == 0 && tot > 0) base_off = atomicAdd(st.pool_ctr, (unsigned long long)tot);
+        base_off = __shfl_sync(kFull, base_off, 0);
+        const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
+        const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
+        if (valid) {
+            st.pool_off[q] = my_off;
+            st.cnt_o[le.pt_off + __ldg(st.perm + q)] = cnt;
+        }
+        __syncwarp();
+        // sort each pooled row: the rank of a key among its row's keys
+        unsigned fm = __ballot_sync(kFull, my_off >= 0);
+        while (fm) {
+            const int i = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int n = __shfl_sync(kFull, deg, i);
+            const int off = __shfl_sync(kFull, my_off, i);
+            const int cnti = __shfl_sync(kFull, cnt, i);
+            const unsigned long long* row = keys + i * kFast;
+            if (lane < n) {
+                const unsigned long long kk = row[lane];
+                int rank = 0;
+                for (int m = 0; m < n; ++m) rank += row[m] < kk;
+                if (rank < cnti) {
+                    st.pool[off + rank] = (int)(unsigned)kk;
+                    if (emit) st.pool_d2[off + rank] = __uint_as_float((unsigned)(kk >> 32));
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Stage 7: rows in CSR order.  Pooled rows are copied; the others (|S_i| >
+// kFast, or no pool space) walk their cell's runs again, one query at a time,
+// keeping the k smallest keys.
+template <int DP4>
+__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(DevState st, int cap)
+{
+    extern __shared__ float4 s_dyn[];
+    constexpr int DP = 4 * DP4;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (32 * DP);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (32 * DP)) + (size_t)wib * cap;
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
@@ -937,136 +997,86 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_fill(De
         const long long q = q0 + lane;
         const bool valid = q < P;
         lane_event(st.ev, B, valid ? q : P - 1, le);
-        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
-        int rs = 0, cnt = 0, dg = 0;
+        int rs = 0, cnt = 0, po = -1;
         if (valid) {
             const long long p = le.pt_off + __ldg(st.perm + q);
             rs = st.row_ptr[p];
             const int re = st.row_ptr[p + 1];
             cnt = ((long long)re <= ecap) ? re - rs : 0;  // over capacity: OVERFLOW already latched
-            dg = st.deg_s[q];
+            po = st.pool_off[q];
         }
-        int nvalid;
-        unsigned seg = stage_chunk<DP4>(st, xs4, q, valid, cs, le.b, sq, lane, &nvalid);
-        const unsigned fast_all = __ballot_sync(kFull, cnt > 0 && dg <= kFast);
-        const unsigned slow_all = __ballot_sync(kFull, cnt > 0 && dg > kFast);
-        int nh = 0;  // keys collected for this lane's query (fast path)
-        while (seg) {
-            const int a = __ffs(seg) - 1;
-            seg &= seg - 1;
-            const int e = seg ? __ffs(seg) - 1 : nvalid;
-            const unsigned smask = (e >= 32 ? kFull : ((1u << e) - 1u)) & ~((1u << a) - 1u);
-            const unsigned fmask = fast_all & smask;
-            unsigned wmask = slow_all & smask;
-            if (!(fmask | wmask)) continue;
-            const int sb = __shfl_sync(kFull, le.b, a);
+        unsigned fm = __ballot_sync(kFull, cnt > 0 && po >= 0);
+        while (fm) {
+            const int i = __ffs(fm) - 1;
+            fm &= fm - 1;
+            const int n = __shfl_sync(kFull, cnt, i);
+            const int src = __shfl_sync(kFull, po, i);
+            const int dst = __shfl_sync(kFull, rs, i);
+            for (int e2 = lane; e2 < n; e2 += 32) {
+                st.col[dst + e2] = st.pool[src + e2];
+                if (emit) st.d2[dst + e2] = st.pool_d2[src + e2];
+            }
+        }
+        unsigned wm = __ballot_sync(kFull, cnt > 0 && po < 0);
+        if (!wm) continue;
+        stage_queries<DP4>(xs4, q, valid, sq, lane);
+        while (wm) {
+            const int i = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int sb = __shfl_sync(kFull, le.b, i);
+            const int rsi = __shfl_sync(kFull, rs, i);
+            const int cnti = __shfl_sync(kFull, cnt, i);
             if (sb != plan_b) {
                 load_seg_plan(st.plan, sb, pl);
                 plan_b = sb;
             }
-            if (pl.skip) continue;
-            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
-            if (fmask) {
-                // pairs that hold at least one fast query
-                const int pa = (__ffs(fmask) - 1) >> 1, pz = (31 - __clz(fmask)) >> 1;
-                for (int base = 0; base < rn.total; base += 32) {
-                    const int cand = candidate_at(rn, base + lane);
-                    CandPk<DP4> cp;
-                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                    const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
-                    const long long cq = (long long)cand - q0;
-                    for (int pp = pa; pp <= pz; ++pp) {
-                        const int i0 = 2 * pp, i1 = 2 * pp + 1;
-                        const bool f0 = (fmask >> i0) & 1u, f1 = (fmask >> i1) & 1u;
-                        if (!(f0 | f1)) continue;
-                        const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
-                        const bool h0 = f0 && cand >= 0 && d.x <= r2 && cq != i0;
-                        const bool h1 = f1 && cand >= 0 && d.y <= r2 && cq != i1;
-                        const unsigned m0 = __ballot_sync(kFull, h0);
-                        const unsigned m1 = __ballot_sync(kFull, h1);
-                        const int b0 = __shfl_sync(kFull, nh, i0);
-                        const int b1 = __shfl_sync(kFull, nh, i1);
-                        if (h0) keys[i0 * kFast + b0 + __popc(m0 & lt_mask)] = edge_key(d.x, j);
-                        if (h1) keys[i1 * kFast + b1 + __popc(m1 & lt_mask)] = edge_key(d.y, j);
-                        if (lane == i0) nh += __popc(m0);
-                        if (lane == i1) nh += __popc(m1);
+            const float* qrow = sq + (i >> 1) * (2 * DP);
+            const int half = i & 1;
+            const Runs rn = segment_runs(pl, qrow, half, st.cell_start, lane);
+            unsigned long long thr = ~0ull;
+            int nk = 0;
+            for (int base = 0; base < rn.total; base += 32) {
+                const int cand = candidate_at(rn, base + lane);
+                unsigned long long key = ~0ull;
+                bool take = false;
+                if (cand >= 0) {
+                    const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
+                    if (d2 <= r2 && (long long)cand != q0 + i) {
+                        key = edge_key(d2, __ldg(st.perm + cand));
+                        take = key < thr;
                     }
                 }
-                __syncwarp();
-                // each collected row: rank of every key among the row's keys
-                unsigned fm = fmask;
-                while (fm) {
-                    const int i = __ffs(fm) - 1;
-                    fm &= fm - 1;
-                    const int n = __shfl_sync(kFull, nh, i);
-                    const int rsi = __shfl_sync(kFull, rs, i);
-                    const int cnti = __shfl_sync(kFull, cnt, i);
-                    const unsigned long long* row = keys + i * kFast;
-                    if (lane < n) {
-                        const unsigned long long kk = row[lane];
-                        int rank = 0;
-                        for (int m = 0; m < n; ++m) rank += row[m] < kk;
-                        if (rank < cnti) {
-                            st.col[rsi + rank] = (int)(unsigned)kk;
-                            if (emit) st.d2[rsi + rank] = __uint_as_float((unsigned)(kk >> 32));
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-            // rows with |S_i| > kFast, one at a time: keep the k smallest keys
-            while (wmask) {
-                const int i = __ffs(wmask) - 1;
-                wmask &= wmask - 1;
-                const int rsi = __shfl_sync(kFull, rs, i);
-                const int cnti = __shfl_sync(kFull, cnt, i);
-                const float* qrow = sq + (i >> 1) * (2 * DP);
-                const int half = i & 1;
-                unsigned long long thr = ~0ull;
-                int nk = 0;
-                for (int base = 0; base < rn.total; base += 32) {
-                    const int cand = candidate_at(rn, base + lane);
-                    unsigned long long key = ~0ull;
-                    bool take = false;
-                    if (cand >= 0) {
-                        const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
-                        if (d2 <= r2 && (long long)cand != q0 + i) {
-                            key = edge_key(d2, __ldg(st.perm + cand));
-                            take = key < thr;
-                        }
-                    }
-                    unsigned m = __ballot_sync(kFull, take);
-                    if (m == 0u) continue;
-                    if (nk + 32 > cap) {
-                        // only reached when |S_i| > k: keep the k smallest so far
-                        warp_sort_smem(keys, nk, lane);
-                        nk = K;
-                        thr = keys[K - 1];
-                        take = take && (key < thr);
-                        m = __ballot_sync(kFull, take);
-                    }
-                    if (take) keys[nk + __popc(m & lt_mask)] = key;
-                    nk += __popc(m);
-                    __syncwarp();
-                }
-                const int nout = min(cnti, nk);
-                if (nk <= 32) {
-                    unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
-                    v = warp_sort32(v, lane);
-                    if (lane < nout) {
-                        st.col[rsi + lane] = (int)(unsigned)v;
-                        if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
-                    }
-                } else {
+                unsigned m = __ballot_sync(kFull, take);
+                if (m == 0u) continue;
+                if (nk + 32 > cap) {
+                    // only reached when |S_i| > k: keep the k smallest so far
                     warp_sort_smem(keys, nk, lane);
-                    for (int e2 = lane; e2 < nout; e2 += 32) {
-                        const unsigned long long v = keys[e2];
-                        st.col[rsi + e2] = (int)(unsigned)v;
-                        if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
-                    }
+                    nk = K;
+                    thr = keys[K - 1];
+                    take = take && (key < thr);
+                    m = __ballot_sync(kFull, take);
                 }
+                if (take) keys[nk + __popc(m & lt_mask)] = key;
+                nk += __popc(m);
                 __syncwarp();
             }
+            const int nout = min(cnti, nk);
+            if (nk <= 32) {
+                unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
+                v = warp_sort32(v, lane);
+                if (lane < nout) {
+                    st.col[rsi + lane] = (int)(unsigned)v;
+                    if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
+                }
+            } else {
+                warp_sort_smem(keys, nk, lane);
+                for (int e2 = lane; e2 < nout; e2 += 32) {
+                    const unsigned long long v = keys[e2];
+                    st.col[rsi + e2] = (int)(unsigned)v;
+                    if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
     }
@@ -1080,24 +1090,26 @@ inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
 }
 
 template <int DP4>
-int count_smem() { return (kWalkThreads / 32) * 32 * 4 * DP4 * (int)sizeof(float); }
+int collect_smem()
+{
+    return (kWalkThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + 32 * kFast * (int)sizeof(unsigned long long));
+}
 
 template <int DP4>
-int fill_smem(int cap)
+int emit_smem(int cap)
 {
-    const int kreg = cap > 32 * kFast ? cap : 32 * kFast;
-    return (kFillThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + kreg * (int)sizeof(unsigned long long));
+    return (kFillThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + cap * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>
 cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t s, cudaEvent_t* ev)
 {
     mark(ev, 4, s);
-    k_walk_count<DP4><<<cfg.grid_count, kWalkThreads, count_smem<DP4>(), s>>>(st);
+    k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
     mark(ev, 5, s);
     k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 6, s);
-    k_walk_fill<DP4><<<cfg.grid_fill, kFillThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
+    k_walk_emit<DP4><<<cfg.grid_fill, kFillThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
     mark(ev, 7, s);
     return cudaGetLastError();
 }
@@ -1105,16 +1117,16 @@ cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t 
 template <int DP4>
 cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
 {
-    const int csm = count_smem<DP4>();
-    const int fsm = fill_smem<DP4>(fill_cap);
-    cudaError_t e = cudaFuncSetAttribute(k_walk_count<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+    const int csm = collect_smem<DP4>();
+    const int fsm = emit_smem<DP4>(fill_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_collect<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_walk_fill<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    e = cudaFuncSetAttribute(k_walk_emit<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     if (e != cudaSuccess) return e;
     int nb_c = 0, nb_f = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_count<DP4>, kWalkThreads, csm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4>, kWalkThreads, csm);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_fill<DP4>, kFillThreads, fsm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_emit<DP4>, kFillThreads, fsm);
     if (e != cudaSuccess) return e;
     cfg->grid_count = n_sm * (nb_c > 0 ? nb_c : 1);
     cfg->grid_fill = n_sm * (nb_f > 0 ? nb_f : 1);
