@@ -845,6 +845,7 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
 // slot per query in shared memory) and sorted there; longer rows are left to
 // the emit walk, which selects the k smallest keys on its own.
 constexpr int kFast = 32;
+constexpr int kRowStride = kFast + 1;  // padded so that lane i's row start falls in bank 2i
 
 // Keys: (bits(d2) << 32) | j.  d2 >= 0, so the 64-bit order is the (d2, j) order.
 __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     float* sq = reinterpret_cast<float*>(s_dyn) + wib * (32 * DP);
     const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(
-        reinterpret_cast<float*>(s_dyn) + (kWalkThreads / 32) * (32 * DP)) + (size_t)wib * (32 * kFast);
+        reinterpret_cast<float*>(s_dyn) + (kWalkThreads / 32) * (32 * DP)) + (size_t)wib * (32 * kRowStride);
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
@@ -918,8 +919,8 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
                     const unsigned m1 = __ballot_sync(kFull, h1);
                     const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
                     const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
-                    if (h0 && s0 < kFast) keys[i0 * kFast + s0] = edge_key(d.x, j);
-                    if (h1 && s1 < kFast) keys[i1 * kFast + s1] = edge_key(d.y, j);
+                    if (h0 && s0 < kFast) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
+                    if (h1 && s1 < kFast) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
                     if (lane == i0) deg += __popc(m0);
                     if (lane == i1) deg += __popc(m1);
                 }
@@ -941,23 +942,32 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
             st.cnt_o[le.pt_off + __ldg(st.perm + q)] = cnt;
         }
         __syncwarp();
-        // sort each pooled row: the rank of a key among its row's keys
+        // every lane sorts its own row (insertion sort, at most kFast keys) ...
+        if (my_off >= 0) {
+            unsigned long long* row = keys + lane * kRowStride;
+            for (int x = 1; x < deg; ++x) {
+                const unsigned long long v = row[x];
+                int y = x - 1;
+                while (y >= 0 && row[y] > v) {
+                    row[y + 1] = row[y];
+                    --y;
+                }
+                row[y + 1] = v;
+            }
+        }
+        __syncwarp();
+        // ... then the rows, cut at k, go to the pool one after another
         unsigned fm = __ballot_sync(kFull, my_off >= 0);
         while (fm) {
             const int i = __ffs(fm) - 1;
             fm &= fm - 1;
-            const int n = __shfl_sync(kFull, deg, i);
             const int off = __shfl_sync(kFull, my_off, i);
             const int cnti = __shfl_sync(kFull, cnt, i);
-            const unsigned long long* row = keys + i * kFast;
-            if (lane < n) {
+            const unsigned long long* row = keys + i * kRowStride;
+            if (lane < cnti) {
                 const unsigned long long kk = row[lane];
-                int rank = 0;
-                for (int m = 0; m < n; ++m) rank += row[m] < kk;
-                if (rank < cnti) {
-                    st.pool[off + rank] = (int)(unsigned)kk;
-                    if (emit) st.pool_d2[off + rank] = __uint_as_float((unsigned)(kk >> 32));
-                }
+                st.pool[off + lane] = (int)(unsigned)kk;
+                if (emit) st.pool_d2[off + lane] = __uint_as_float((unsigned)(kk >> 32));
             }
         }
         __syncwarp();
@@ -1005,16 +1015,28 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
             cnt = ((long long)re <= ecap) ? re - rs : 0;  // over capacity: OVERFLOW already latched
             po = st.pool_off[q];
         }
-        unsigned fm = __ballot_sync(kFull, cnt > 0 && po >= 0);
-        while (fm) {
-            const int i = __ffs(fm) - 1;
-            fm &= fm - 1;
-            const int n = __shfl_sync(kFull, cnt, i);
-            const int src = __shfl_sync(kFull, po, i);
-            const int dst = __shfl_sync(kFull, rs, i);
-            for (int e2 = lane; e2 < n; e2 += 32) {
-                st.col[dst + e2] = st.pool[src + e2];
-                if (emit) st.d2[dst + e2] = st.pool_d2[src + e2];
+        // pooled rows: the chunk's rows lie back to back in the pool, in lane
+        // order, so the warp streams them with coalesced loads
+        {
+            const bool pooled = cnt > 0 && po >= 0;
+            const int need = pooled ? cnt : 0;
+            const int incl = warp_incl_scan(need, lane);
+            const int tot = __shfl_sync(kFull, incl, 31);
+            if (tot > 0) {
+                // element e of the chunk's list belongs to lane r = find_run(incl, e)
+                const int rel = rs - (incl - need);  // its destination: rel_r + e
+                const int srel = po - (incl - need);  // its pool slot: srel_r + e
+#pragma unroll 2
+                for (int base = 0; base < tot; base += 32) {
+                    const int e2 = base + lane;
+                    const int r = find_run(incl, e2);
+                    const int dst = __shfl_sync(kFull, rel, r) + e2;
+                    const int src = __shfl_sync(kFull, srel, r) + e2;
+                    if (e2 < tot) {
+                        st.col[dst] = st.pool[src];
+                        if (emit) st.d2[dst] = st.pool_d2[src];
+                    }
+                }
             }
         }
         unsigned wm = __ballot_sync(kFull, cnt > 0 && po < 0);
@@ -1092,7 +1114,7 @@ inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
 template <int DP4>
 int collect_smem()
 {
-    return (kWalkThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + 32 * kFast * (int)sizeof(unsigned long long));
+    return (kWalkThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + 32 * kRowStride * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>
