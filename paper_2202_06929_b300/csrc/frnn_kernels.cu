@@ -845,7 +845,8 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
 // slot per query in shared memory) and sorted there; longer rows are left to
 // the emit walk, which selects the k smallest keys on its own.
 constexpr int kFast = 32;
-constexpr int kRowStride = kFast + 1;  // padded so that lane i's row start falls in bank 2i
+constexpr int kRowSlots = kFast + 1;   // a row also holds the query's own key while collecting
+constexpr int kRowStride = kFast + 1;  // = kRowSlots; odd, so row starts of lanes 0..15 fall in distinct banks
 
 // Keys: (bits(d2) << 32) | j.  d2 >= 0, so the 64-bit order is the (d2, j) order.
 __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
@@ -908,25 +909,31 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
                 CandPk<DP4> cp;
                 load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
                 const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
-                const long long cq = (long long)cand - q0;  // candidate's lane if it is in this chunk
+                const bool cv = cand >= 0;
+                // Every query meets itself exactly once (d2 = 0): it is counted
+                // here and taken out below, which keeps a self test out of this loop.
 #pragma unroll 2
                 for (int pp = p0; pp < p1; ++pp) {
                     const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
                     const int i0 = 2 * pp, i1 = 2 * pp + 1;
-                    const bool h0 = cand >= 0 && d.x <= r2 && cq != i0 && i0 >= a;
-                    const bool h1 = cand >= 0 && d.y <= r2 && cq != i1 && i1 < e;
+                    const bool h0 = cv && (i0 >= a) && d.x <= r2;
+                    const bool h1 = cv && (i1 < e) && d.y <= r2;
                     const unsigned m0 = __ballot_sync(kFull, h0);
                     const unsigned m1 = __ballot_sync(kFull, h1);
-                    const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
-                    const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
-                    if (h0 && s0 < kFast) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
-                    if (h1 && s1 < kFast) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
-                    if (lane == i0) deg += __popc(m0);
-                    if (lane == i1) deg += __popc(m1);
+                    if (m0 | m1) {
+                        const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
+                        const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
+                        if (h0 && s0 < kRowSlots) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
+                        if (h1 && s1 < kRowSlots) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
+                        if (lane == i0) deg += __popc(m0);
+                        if (lane == i1) deg += __popc(m1);
+                    }
                 }
             }
         }
         // pool space for the chunk's short rows
+        const int raw = deg;                 // includes the query itself
+        deg = raw > 0 ? raw - 1 : 0;         // |S_i|
         const int cnt = min(deg, K);
         const bool fast = valid && deg > 0 && deg <= kFast;
         const int need = fast ? cnt : 0;
@@ -937,16 +944,22 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
         base_off = __shfl_sync(kFull, base_off, 0);
         const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
         const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
+        const int self_j = valid ? __ldg(st.perm + q) : -1;
         if (valid) {
             st.pool_off[q] = my_off;
-            st.cnt_o[le.pt_off + __ldg(st.perm + q)] = cnt;
+            st.cnt_o[le.pt_off + self_j] = cnt;
         }
         __syncwarp();
-        // every lane sorts its own row (insertion sort, at most kFast keys) ...
+        // every lane sorts its own row (insertion sort, at most kRowSlots keys);
+        // the query's own key (d2 = 0, j = itself) is set to the largest value
+        // first, so that it sorts last and the first |S_i| keys are the row ...
         if (my_off >= 0) {
             unsigned long long* row = keys + lane * kRowStride;
-            for (int x = 1; x < deg; ++x) {
-                const unsigned long long v = row[x];
+            const unsigned long long self_key = (unsigned long long)(unsigned)self_j;
+            if (row[0] == self_key) row[0] = ~0ull;
+            for (int x = 1; x < raw; ++x) {
+                unsigned long long v = row[x];
+                if (v == self_key) v = ~0ull;
                 int y = x - 1;
                 while (y >= 0 && row[y] > v) {
                     row[y + 1] = row[y];
