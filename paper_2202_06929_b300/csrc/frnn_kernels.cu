@@ -1154,9 +1154,12 @@ cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
 {
     const int csm = collect_smem<DP4>();
     const int fsm = emit_smem<DP4>(fill_cap);
+    // The attribute is a per-kernel upper bound shared by every plan in the
+    // process, so it is set to the largest size any cap (k <= 1024) can need,
+    // never lowered to this plan's size.
     cudaError_t e = cudaFuncSetAttribute(k_walk_collect<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_walk_emit<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    e = cudaFuncSetAttribute(k_walk_emit<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
     if (e != cudaSuccess) return e;
     int nb_c = 0, nb_f = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4>, kWalkThreads, csm);

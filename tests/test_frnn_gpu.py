@@ -317,3 +317,21 @@ def test_c2_batched_bench_configuration():
             _check_sampled(evs[b], 0.1, 256, rp, col, _sample_queries(evs[b].shape[0], 150, b))
     finally:
         plan.close()
+
+
+def test_plans_with_different_caps_coexist():
+    """A plan with a small cap must not shrink the shared-memory limit that a
+    plan with k = 1024 (the largest per-warp key buffer) launches with."""
+    x = synth.uniform_grid(3000, 2, 23, -30, 30)
+    big = frnn.Plan(n_max=3000, d_max=2, k_max_cap=1024)
+    small = frnn.Plan(n_max=3000, d_max=2, k_max_cap=32)
+    try:
+        rp, col = oracle.radius_graph(x, 0.06, 1024)
+        rps, cols = oracle.radius_graph(x, 0.06, 32)
+        for plan, k, want in [(big, 1024, col), (small, 32, cols), (big, 1024, col)]:
+            host, st = gpu_csr(x, 0.06, k, plan=plan)
+            assert st == 0
+            np.testing.assert_array_equal(host["col"], want)
+    finally:
+        big.close()
+        small.close()
