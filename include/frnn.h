@@ -183,6 +183,36 @@ FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const 
  */
 FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
 
+/*
+ * Build the graph of one event without allocating any device memory.  The
+ * paper has no counterpart: this is for callers that may not call cudaMalloc
+ * (code running inside a framework that owns all device memory and forbids
+ * allocation after start-up, or whose device memory is fixed at
+ * initialisation).  The caller passes the points and the outputs; every other
+ * buffer lives in one array of about 11.5 MB in device memory that each
+ * device loading the library holds until the process exits.
+ *   emb          device float32 [n][d], row-major, caller-owned.
+ *   n <= 32768, d <= 16, k_max <= 64; larger sizes return FRNN_ERR_CAPACITY
+ *                (nothing is enqueued).
+ *   row_ptr      device int32 [n + 1], receives the row offsets.
+ *   col          device int32 [col_capacity], receives the rows (event-local
+ *                indices, in increasing (d2, j) order, as frnn_build_graph).
+ *   status       device int32, receives the device-side outcome: FRNN_OK,
+ *                FRNN_ERR_NONFINITE_INPUT, FRNN_ERR_OVERFLOW (more edges than
+ *                col_capacity) or FRNN_ERR_TIMEOUT.
+ *   stream       cudaStream_t; asynchronous, no host synchronisation.
+ * Runs on the calling thread's current device.  The first call on a device
+ * looks up the array's device address and the launch shapes; make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Each call clears what must
+ * start at zero, so results never depend on an earlier call.
+ * Returns FRNN_OK, FRNN_ERR_INVALID_ARG, FRNN_ERR_CAPACITY or FRNN_ERR_CUDA.
+ */
+FRNN_API int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, float r, int k_max,
+                                      int32_t* row_ptr, int32_t* col, int64_t col_capacity,
+                                      int32_t* status, void* stream);
+
 /* Static English description of a status code (never NULL). */
 FRNN_API const char* frnn_status_string(int status);
 

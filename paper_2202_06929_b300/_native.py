@@ -30,7 +30,7 @@ FRNN_USE_GRAPH = 0x2
 ABI_FUNCTIONS = (
     "frnn_plan_create", "frnn_plan_destroy", "frnn_plan_set_tuning", "frnn_plan_get_tuning",
     "frnn_build_graph", "frnn_build_graph_batched", "frnn_build_graph_host", "frnn_build_graph_profiled",
-    "frnn_get_last_status", "frnn_status_string", "frnn_version",
+    "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
 )
 
 
