@@ -59,6 +59,9 @@ def parse_args(argv=None):
                     help="queries of the CPU oracle sample (bounded CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=2000,
+                    help="measured requests per offered load (plus 200 warm-up)")
     return ap.parse_args(argv)
 
 
@@ -246,6 +249,48 @@ def reference_arm(args, rank, world):
     return 0
 
 
+# --------------------------------------------------------------------------- served
+
+def run_served(frnn, torch, n_requests: int, pool_events: int = 48, seed: int = 7):
+    """Served workload: events of N ~ U[20k, 200k] (the N=120k generator),
+    D=8, r=0.1, K=256, Poisson arrivals at 0.25x..1.5x of the measured
+    capacity, continuous batching on 3 slots within a 40 GB device budget.
+    Requests draw from a pool of distinct events (seeded)."""
+    evs = [synth.make_event("c4", e) for e in range(pool_events)]
+    sizes = np.array([e.shape[0] for e in evs], dtype=np.int64)
+    start = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    x_all = torch.from_numpy(np.concatenate(evs)).pin_memory().numpy()
+    rng = np.random.default_rng(seed)
+    warm = 200
+    req = rng.integers(0, pool_events, size=warm + n_requests)
+    srv = frnn.Server(d=D, r=R, k=K, batch_points=2_000_000, batch_events=64, slots=3, edges_per_point=32,
+                      mem_budget_bytes=40 << 30)
+    try:
+        # capacity: every request present at t = 0
+        sat = srv.run_trace(x_all, start[req], sizes[req], np.zeros(req.size))
+        capacity = req.size / sat["wall_s"]
+        loads = []
+        for f in (0.25, 0.5, 1.0, 1.5):
+            rate = f * capacity
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=req.size))
+            arr -= arr[0]
+            res = srv.run_trace(x_all, start[req], sizes[req], arr)
+            lat = res["latency_s"][warm:] * 1e3
+            span = arr[-1] - arr[warm] if req.size > warm + 1 else res["wall_s"]
+            done_eps = n_requests / max(res["wall_s"] - arr[warm], 1e-9)
+            loads.append({"offered_x_capacity": f, "offered_events_per_s": rate,
+                          "achieved_events_per_s": done_eps, "latency_ms_p50": percentile(lat, 50),
+                          "latency_ms_p99": percentile(lat, 99), "arrival_span_s": span})
+        return {"workload": "c4: N ~ U[20000, 200000] per event, D=8, r=0.1, K=256, Poisson arrivals",
+                "requests_per_load": n_requests, "warmup_requests": warm, "event_pool": pool_events,
+                "slots": 3, "batch_points": 2_000_000, "mem_budget_gb": 40,
+                "reserved_gb": srv.reserved_bytes() / 1e9,
+                "capacity_events_per_s": capacity, "loads": loads,
+                "latency_note": "arrival (host clock) to the event's CSR on the host"}
+    finally:
+        srv.close()
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main(argv=None):
@@ -363,6 +408,11 @@ def main(argv=None):
                        "row_ptr, edge_off and col, host wall clock"}
         del ctypes
 
+    # ---- served (continuous batching), rank 0 at N=1 only
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = run_served(frnn, torch, args.served_requests)
+
     # ---- CPU oracle baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -400,6 +450,7 @@ def main(argv=None):
                                          "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
                                          "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak}},
             "e2e": e2e,
+            "served": served,
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_BUILD * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],

@@ -111,6 +111,13 @@ typedef struct {
  */
 FRNN_API int frnn_plan_create(frnn_plan** out, const frnn_plan_params* p);
 
+/*
+ * Device bytes frnn_plan_create would allocate for these parameters (the
+ * footprint a serving layer budgets for).  Errors: INVALID_ARG as
+ * frnn_plan_create.
+ */
+FRNN_API int frnn_plan_bytes(const frnn_plan_params* p, uint64_t* bytes);
+
 /* Free every buffer of the plan (synchronises its device).  NULL is a no-op. */
 FRNN_API int frnn_plan_destroy(frnn_plan* plan);
 
@@ -212,6 +219,76 @@ FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
 FRNN_API int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, float r, int k_max,
                                       int32_t* row_ptr, int32_t* col, int64_t col_capacity,
                                       int32_t* status, void* stream);
+
+/*
+ * Serving: events arriving over time, built with continuous batching.
+ * (The paper runs the pipeline per event inside a multithreaded C++ host,
+ * Sec. 4, and names a model server as future work, Sec. 6.)  A server owns
+ * `slots` plans, each with its own stream and its device memory reserved at
+ * creation; a dispatcher thread starts a batched build on every free slot with
+ * the requests that have arrived and not started, in arrival order, as many
+ * as fit (batch_points points, batch_events events).  Batches on different
+ * slots overlap on the device, and requests arriving meanwhile are admitted
+ * as slots free up.  Each request's rows are identical to a separate
+ * frnn_build_graph of the same points.
+ */
+typedef struct frnn_server frnn_server;
+
+typedef struct {
+    int device;
+    int d;                     /* embedding dimension of every request, 1..64        */
+    float r;                   /* radius (finite, > 0)                                */
+    int k;                     /* neighbour cap, 1..1024                              */
+    int64_t batch_points;      /* points of one batched launch (also the largest event) */
+    int batch_events;          /* events of one batched launch                        */
+    int slots;                 /* batches in flight at once, 1..64                    */
+    int edges_per_point;       /* edge capacity of a slot per point (0 = min(32, k))  */
+    uint64_t mem_budget_bytes; /* device memory all slots may reserve (0 = no limit) */
+} frnn_server_params;
+
+/*
+ * Create a server and its dispatcher thread.  Device memory of all slots is
+ * reserved here: FRNN_ERR_OOM if it exceeds mem_budget_bytes (or the device).
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+FRNN_API int frnn_server_create(frnn_server** out, const frnn_server_params* p);
+
+/* Device bytes the server reserved for its slots. */
+FRNN_API int frnn_server_reserved_bytes(const frnn_server* srv, uint64_t* bytes);
+
+/*
+ * Queue one event (host float32 [n][d]; the buffer must stay valid and
+ * unchanged until frnn_server_wait returns for this ticket; pinned memory
+ * copies faster).  Returns at once.  Errors: INVALID_ARG, CAPACITY
+ * (n > batch_points), OOM.
+ */
+FRNN_API int frnn_server_submit(frnn_server* srv, const float* host_emb, int64_t n, uint64_t* ticket);
+
+/*
+ * Block until the event of `ticket` is built, then copy its CSR (event-local
+ * indices) to host buffers: row_ptr [n + 1], col [col_capacity].  *n_edges
+ * and *latency_s (arrival to rows on the host) may be NULL.  Each ticket can
+ * be waited for once.  Returns the event's status (OVERFLOW if col_capacity
+ * is too small, or if the slot's edge capacity was exceeded).
+ */
+FRNN_API int frnn_server_wait(frnn_server* srv, uint64_t ticket, int32_t* row_ptr, int32_t* col,
+                              int64_t col_capacity, int64_t* n_edges, double* latency_s);
+
+/*
+ * Replay an arrival trace through the server: request i, the points
+ * host_emb[ev_start[i] .. ev_start[i] + ev_len[i]) (rows of d floats; requests
+ * may share points), is submitted arrival_s[i] seconds (non-decreasing) after
+ * the call starts, by the calling thread.  Returns when every request is done;
+ * latency_s[i] (arrival to rows on the host), n_edges[i] (may be NULL) and
+ * *wall_s (may be NULL) are filled in.  The rows themselves are not kept.
+ * Returns the first non-OK request status.
+ */
+FRNN_API int frnn_server_run_trace(frnn_server* srv, const float* host_emb, const int64_t* ev_start,
+                                   const int64_t* ev_len, const double* arrival_s, int n_events,
+                                   double* latency_s, int64_t* n_edges, double* wall_s);
+
+/* Finish queued work, stop the dispatcher and free everything.  NULL is a no-op. */
+FRNN_API int frnn_server_destroy(frnn_server* srv);
 
 /* Static English description of a status code (never NULL). */
 FRNN_API const char* frnn_status_string(int status);

@@ -31,6 +31,8 @@ ABI_FUNCTIONS = (
     "frnn_plan_create", "frnn_plan_destroy", "frnn_plan_set_tuning", "frnn_plan_get_tuning",
     "frnn_build_graph", "frnn_build_graph_batched", "frnn_build_graph_host", "frnn_build_graph_profiled",
     "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
+    "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
+    "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy",
 )
 
 
@@ -49,6 +51,12 @@ class frnn_csr(ctypes.Structure):
 
 class frnn_tuning(ctypes.Structure):
     _fields_ = [("g_max", ctypes.c_int), ("cell_scale", ctypes.c_float)]
+
+
+class frnn_server_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_float), ("k", ctypes.c_int),
+                ("batch_points", ctypes.c_int64), ("batch_events", ctypes.c_int), ("slots", ctypes.c_int),
+                ("edges_per_point", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64)]
 
 
 _lib = None
@@ -79,6 +87,15 @@ def load():
                                           vp, P(ctypes.c_int64), vp]
     lib.frnn_build_graph_profiled.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp,
                                               P(frnn_csr), P(ctypes.c_float), i32]
+    lib.frnn_plan_bytes.argtypes = [P(frnn_plan_params), P(ctypes.c_uint64)]
+    lib.frnn_server_create.argtypes = [P(vp), P(frnn_server_params)]
+    lib.frnn_server_reserved_bytes.argtypes = [vp, P(ctypes.c_uint64)]
+    lib.frnn_server_submit.argtypes = [vp, vp, i64, P(ctypes.c_uint64)]
+    lib.frnn_server_wait.argtypes = [vp, ctypes.c_uint64, vp, vp, i64, P(ctypes.c_int64), P(ctypes.c_double)]
+    lib.frnn_server_run_trace.argtypes = [vp, vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_double), i32,
+                                          P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double)]
+    lib.frnn_server_destroy.argtypes = [vp]
+    lib.frnn_build_graph_noalloc.argtypes = [vp, i64, i32, f32, i32, vp, vp, i64, vp, vp]
     lib.frnn_get_last_status.argtypes = [vp, vp]
     lib.frnn_status_string.argtypes = [i32]
     lib.frnn_status_string.restype = ctypes.c_char_p
@@ -305,3 +322,98 @@ class Plan:
 
     def check(self, stream=None) -> None:
         _check(self.last_status(stream), "device status")
+
+
+def plan_bytes(n_max: int, d_max: int, k_max_cap: int, events_max: int = 1, edge_capacity: int = 0,
+               cells_per_point: int = 0, emit_d2: bool = False) -> int:
+    """Device bytes a plan with these capacities allocates (frnn_plan_bytes)."""
+    prm = frnn_plan_params(device=0, d_max=d_max, n_max=n_max, events_max=events_max, k_max_cap=k_max_cap,
+                           edge_capacity=edge_capacity, cells_per_point=cells_per_point,
+                           flags=FRNN_EMIT_D2 if emit_d2 else 0)
+    b = ctypes.c_uint64(0)
+    _check(load().frnn_plan_bytes(ctypes.byref(prm), ctypes.byref(b)), "frnn_plan_bytes")
+    return int(b.value)
+
+
+class Server:
+    """Continuous-batching graph server (frnn_server_*): submit host events,
+    wait for their CSR; batches run on `slots` concurrent streams."""
+
+    def __init__(self, d: int, r: float, k: int, batch_points: int, batch_events: int = 64, slots: int = 2,
+                 edges_per_point: int = 0, mem_budget_bytes: int = 0, device: int = 0):
+        lib = load()
+        prm = frnn_server_params(device=device, d=d, r=r, k=k, batch_points=batch_points,
+                                 batch_events=batch_events, slots=slots, edges_per_point=edges_per_point,
+                                 mem_budget_bytes=mem_budget_bytes)
+        h = ctypes.c_void_p()
+        _check(lib.frnn_server_create(ctypes.byref(h), ctypes.byref(prm)), "frnn_server_create")
+        self._h = h
+        self.d, self.k = d, k
+        self._held = {}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            load().frnn_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._held = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reserved_bytes(self) -> int:
+        b = ctypes.c_uint64(0)
+        _check(load().frnn_server_reserved_bytes(self._h, ctypes.byref(b)), "frnn_server_reserved_bytes")
+        return int(b.value)
+
+    def submit(self, x: np.ndarray) -> int:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        if x.ndim != 2 or x.shape[1] != self.d:
+            raise ValueError("x must be [n, d]")
+        t = ctypes.c_uint64(0)
+        _check(load().frnn_server_submit(self._h, x.ctypes.data, x.shape[0], ctypes.byref(t)), "frnn_server_submit")
+        self._held[int(t.value)] = x  # the server reads it until the event is done
+        return int(t.value)
+
+    def wait(self, ticket: int) -> dict:
+        x = self._held.pop(ticket)
+        n = x.shape[0]
+        row_ptr = np.zeros(n + 1, np.int32)
+        col = np.zeros(max(n * self.k, 1), np.int32)
+        ne = ctypes.c_int64(0)
+        lat = ctypes.c_double(0.0)
+        rc = load().frnn_server_wait(self._h, ticket, row_ptr.ctypes.data, col.ctypes.data, col.size,
+                                     ctypes.byref(ne), ctypes.byref(lat))
+        _check(rc, "frnn_server_wait")
+        return dict(row_ptr=row_ptr, col=col[:ne.value], n_edges=int(ne.value), latency_s=float(lat.value))
+
+    def run_trace(self, x_all: np.ndarray, ev_start, ev_len, arrival_s) -> dict:
+        """Replay arrivals (seconds from the start, non-decreasing).  Request i
+        is the points x_all[ev_start[i] : ev_start[i] + ev_len[i]] (requests may
+        share points; pinned memory copies faster)."""
+        if not (isinstance(x_all, np.ndarray) and x_all.dtype == np.float32 and x_all.flags["C_CONTIGUOUS"]):
+            x_all = np.ascontiguousarray(x_all, dtype=np.float32)
+        st = np.ascontiguousarray(ev_start, dtype=np.int64)
+        ln = np.ascontiguousarray(ev_len, dtype=np.int64)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        if not (st.size == ln.size == arr.size) or (st.size and (st + ln).max() > x_all.shape[0]):
+            raise ValueError("ev_start, ev_len and arrival_s must have one entry per request inside x_all")
+        n_ev = st.size
+        lat = np.zeros(n_ev, np.float64)
+        ne = np.zeros(n_ev, np.int64)
+        wall = ctypes.c_double(0.0)
+        P = ctypes.POINTER
+        rc = load().frnn_server_run_trace(self._h, x_all.ctypes.data, st.ctypes.data_as(P(ctypes.c_int64)),
+                                          ln.ctypes.data_as(P(ctypes.c_int64)), arr.ctypes.data_as(P(ctypes.c_double)),
+                                          n_ev, lat.ctypes.data_as(P(ctypes.c_double)),
+                                          ne.ctypes.data_as(P(ctypes.c_int64)), ctypes.byref(wall))
+        _check(rc, "frnn_server_run_trace")
+        return dict(latency_s=lat, n_edges=ne, wall_s=float(wall.value))

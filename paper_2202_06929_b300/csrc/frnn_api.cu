@@ -268,6 +268,45 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     return FRNN_OK;
 }
 
+// Checks plan parameters and fills in their defaults.
+int normalize_params(const frnn_plan_params* prm, frnn_plan_params* out, long long* cells_max)
+{
+    frnn_plan_params q = *prm;
+    if (q.d_max < 1 || q.d_max > kMaxDims || q.n_max < 0 || q.events_max < 1 ||
+        q.k_max_cap < 1 || q.k_max_cap > 1024 || q.edge_capacity < 0 || q.cells_per_point < 0)
+        return FRNN_ERR_INVALID_ARG;
+    if (q.cells_per_point == 0) q.cells_per_point = 4;
+    if (q.edge_capacity == 0) {
+        if (q.n_max * (long long)q.k_max_cap >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+        q.edge_capacity = q.n_max * (long long)q.k_max_cap;
+    }
+    if (q.edge_capacity >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+    const long long cm = q.cells_per_point * q.n_max + 4096ll * q.events_max;
+    if (cm >= (1ll << 31) || q.n_max >= (1ll << 31) - 1) return FRNN_ERR_INVALID_ARG;
+    *out = q;
+    *cells_max = cm;
+    return FRNN_OK;
+}
+
+// Device bytes frnn_plan_create allocates for these (normalised) parameters.
+unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_max)
+{
+    const unsigned long long n = (unsigned long long)q.n_max, ev = (unsigned long long)q.events_max;
+    const unsigned long long dp = (unsigned long long)((q.d_max + 3) & ~3);
+    const unsigned long long ec = (unsigned long long)q.edge_capacity;
+    const unsigned long long tiles_c = (unsigned long long)(cells_max + kScanTile - 1) / kScanTile + 1;
+    const unsigned long long tiles_r = (n + kScanTile - 1) / kScanTile + 1;
+    const bool d2 = (q.flags & FRNN_EMIT_D2) != 0;
+    unsigned long long b = sizeof(CallHdr) + sizeof(EvDesc) * ev + sizeof(EvPlan) * ev;
+    b += 2 * sizeof(unsigned) * ev * kMaxDims + 2 * sizeof(unsigned) * ev + sizeof(unsigned) * kCtrCount + 4;
+    b += 4 * sizeof(unsigned) * n + sizeof(float) * n * dp + 2 * sizeof(int) * n + sizeof(int) * (n + 1);
+    b += sizeof(unsigned) * (unsigned long long)cells_max + sizeof(int) * ((unsigned long long)cells_max + 1);
+    b += sizeof(unsigned long long) * (tiles_c + tiles_r);
+    b += sizeof(int) * ec * 2 + (d2 ? 2 * sizeof(float) * ec : 0);
+    b += 8 + sizeof(int) * (ev + 1) + 4;
+    return b;
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,22 +328,25 @@ const char* frnn_status_string(int status)
     }
 }
 
+int frnn_plan_bytes(const frnn_plan_params* prm, uint64_t* bytes)
+{
+    if (!prm || !bytes) return FRNN_ERR_INVALID_ARG;
+    frnn_plan_params q;
+    long long cm = 0;
+    const int rc = normalize_params(prm, &q, &cm);
+    if (rc != FRNN_OK) return rc;
+    *bytes = plan_device_bytes(q, cm);
+    return FRNN_OK;
+}
+
 int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
 {
     if (!out || !prm) return FRNN_ERR_INVALID_ARG;
     *out = nullptr;
-    frnn_plan_params q = *prm;
-    if (q.d_max < 1 || q.d_max > kMaxDims || q.n_max < 0 || q.events_max < 1 ||
-        q.k_max_cap < 1 || q.k_max_cap > 1024 || q.edge_capacity < 0 || q.cells_per_point < 0)
-        return FRNN_ERR_INVALID_ARG;
-    if (q.cells_per_point == 0) q.cells_per_point = 4;
-    if (q.edge_capacity == 0) {
-        if (q.n_max * (long long)q.k_max_cap >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
-        q.edge_capacity = q.n_max * (long long)q.k_max_cap;
-    }
-    if (q.edge_capacity >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
-    const long long cells_max = q.cells_per_point * q.n_max + 4096ll * q.events_max;
-    if (cells_max >= (1ll << 31) || q.n_max >= (1ll << 31) - 1) return FRNN_ERR_INVALID_ARG;
+    frnn_plan_params q;
+    long long cells_max = 0;
+    const int nrc = normalize_params(prm, &q, &cells_max);
+    if (nrc != FRNN_OK) return nrc;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || q.device < 0 || q.device >= n_dev) {
         cudaGetLastError();
