@@ -46,6 +46,10 @@ N_PER_EVENT, D, R, K = 120_000, 8, 0.1, 256
 KERNELS_PER_BUILD = 7
 STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
 L2_BYTES = 126 * 1024 * 1024
+# DRAM read + write bytes per point of the collect walk, from the ncu capture
+# summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
+# kernel source it was taken on (traffic scales with the points processed).
+MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "42e62d75880b", "bytes_per_point": 429_538_816 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -187,6 +191,19 @@ def measured_peaks():
         return float(m["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6400.0, "fallback"
+
+
+def measured_traffic(stage: str, n_total: int):
+    """roofline.traffic of the given stage, or None once the kernel source changed."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2202_06929_b300", "csrc", "frnn_kernels.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if stage != MEASURED_TRAFFIC["stage"] or not sha.startswith(MEASURED_TRAFFIC["source_sha1_prefix"]):
+        return None
+    return MEASURED_TRAFFIC["bytes_per_point"] * n_total
 
 
 def stage_bytes(n_total: int, n_edges: int, d: int):
@@ -443,7 +460,7 @@ def main(argv=None):
             "stages_ms": stage_avg,
             "roofline": {"bound": "hbm", "kernel": "k_" + dom,
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": None, "peak_kind": peak_kind,
+                         "traffic": measured_traffic(dom, n_total), "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": sbytes[dom],
                          "launch_ms": stage_avg[dom],
                          "whole_build": {"algorithmic_bytes": whole_bytes,
