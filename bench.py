@@ -57,7 +57,11 @@ def parse_args(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--events", type=int, default=64, help="events per batched step")
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "c5b"], default="c2",
+                    help="c2: N=120k events (the headline); c3: N~U[40k,140k], K=64; "
+                         "c5/c5b: N=1M, D=12, r=0.15, K=128 (c5b: the cap binds)")
+    ap.add_argument("--events", type=int, default=None, help="events per batched step (64; 8 for c5/c5b)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-queries", type=int, default=40_000,
                     help="queries of the CPU oracle sample (bounded CPU work)")
@@ -111,9 +115,9 @@ def sum_over_ranks(pg, value: float, device=None) -> float:
 
 # --------------------------------------------------------------------------- workload
 
-def make_batch(rank: int, n_events: int):
-    """Events rank*n_events .. of the N=120k workload, concatenated."""
-    evs = [synth.make_event("c2", rank * n_events + e) for e in range(n_events)]
+def make_batch(rank: int, n_events: int, workload: str = "c2"):
+    """Events rank*n_events .. of a workload, concatenated (ranks never share events)."""
+    evs = [synth.make_event(workload, rank * n_events + e) for e in range(n_events)]
     off = np.zeros(n_events + 1, dtype=np.int64)
     off[1:] = np.cumsum([e.shape[0] for e in evs])
     return np.ascontiguousarray(np.concatenate(evs)), off
@@ -225,12 +229,12 @@ def stage_bytes(n_total: int, n_edges: int, d: int):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def run_cpu_baseline(x, queries: int, seed: int = 0):
+def run_cpu_baseline(x, queries: int, seed: int = 0, r: float = R, k: int = K):
     import oracle
     n = x.shape[0]
     q = np.random.default_rng(seed).choice(n, size=min(queries, n), replace=False)
     t0 = time.perf_counter()
-    oracle.radius_graph(x, R, K, queries=q)
+    oracle.radius_graph(x, r, k, queries=q)
     dt = time.perf_counter() - t0
     return {"value": (len(q) / n) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{len(q)} random query rows of one N={n} event (brute force over all {n} points), "
@@ -324,32 +328,46 @@ def main(argv=None):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    B = args.events
-    x_host, off = make_batch(rank, B)
+    wl = synth.WORKLOADS[args.workload]
+    d, r, k = wl.d, wl.r, wl.k
+    B = args.events or (8 if args.workload in ("c5", "c5b") else 64)
+    x_host, off = make_batch(rank, B, args.workload)
     n_total = int(off[-1])
+    n_max_event = int(np.max(np.diff(off)))
     x_dev = torch.from_numpy(x_host).to(dev)
     stream = torch.cuda.Stream(device=dev)
+    epp = k if args.workload == "c5b" else 64  # edge slots per point (C5b rows hold up to K)
 
-    plan = frnn.Plan(n_max=n_total, d_max=D, k_max_cap=K, events_max=B, edge_capacity=n_total * 64,
+    plan = frnn.Plan(n_max=n_total, d_max=d, k_max_cap=k, events_max=B, edge_capacity=n_total * epp,
                      use_graph=True, device=local)
-    plan_one = frnn.Plan(n_max=N_PER_EVENT, d_max=D, k_max_cap=K, events_max=1,
-                         edge_capacity=N_PER_EVENT * 64, use_graph=True, device=local)
+    plan_one = frnn.Plan(n_max=n_max_event, d_max=d, k_max_cap=k, events_max=1,
+                         edge_capacity=n_max_event * epp, use_graph=True, device=local)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            g, scale, ms = plan.autotune(x_dev, off, r, k, stream=stream)
+            g1, scale1, ms1 = plan_one.autotune(x_dev[int(off[0]):int(off[1])], off[:2], r, k, stream=stream)
+        tuned = {"batched": {"g_max": g, "cell_scale": scale, "build_ms": ms},
+                 "plain": {"g_max": g1, "cell_scale": scale1, "build_ms": ms1},
+                 "seconds": time.perf_counter() - t0,
+                 "searched": "g_max in {4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each"}
 
     # ---- batched: the timed step
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            plan.build_batched(x_dev, off, R, K, stream=stream)
+            plan.build_batched(x_dev, off, r, k, stream=stream)
         st = plan.last_status(stream)
         if st != 0:
             raise RuntimeError(f"warm-up status: {frnn.status_string(st)}")
-        n_edges = int(plan.build_batched(x_dev, off, R, K, stream=stream).n_edges())
+        n_edges = int(plan.build_batched(x_dev, off, r, k, stream=stream).n_edges())
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         barrier(pg)
         torch.cuda.synchronize(dev)
         with ClockSampler(local) as clk:
             ev[0].record(stream)
             for i in range(args.steps):
-                plan.build_batched(x_dev, off, R, K, stream=stream)
+                plan.build_batched(x_dev, off, r, k, stream=stream)
                 ev[i + 1].record(stream)
             torch.cuda.synchronize(dev)
         barrier(pg)
@@ -368,13 +386,13 @@ def main(argv=None):
     with torch.cuda.stream(stream):
         for e in range(min(B, 4)):
             lo, hi = int(off[e]), int(off[e + 1])
-            plan_one.build(x_dev[lo:hi], R, K, stream=stream)
+            plan_one.build(x_dev[lo:hi], r, k, stream=stream)
         pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * B)]
         torch.cuda.synchronize(dev)
         for e in range(B):
             lo, hi = int(off[e]), int(off[e + 1])
             pe[2 * e].record(stream)
-            plan_one.build(x_dev[lo:hi], R, K, stream=stream)
+            plan_one.build(x_dev[lo:hi], r, k, stream=stream)
             pe[2 * e + 1].record(stream)
         torch.cuda.synchronize(dev)
         plain_ms = [pe[2 * e].elapsed_time(pe[2 * e + 1]) for e in range(B)]
@@ -388,15 +406,15 @@ def main(argv=None):
     stage_ms = {s: [] for s in STAGES}
     with torch.cuda.stream(stream):
         for _ in range(5):
-            _, ms = plan.build_profiled(x_dev, off, R, K, stream=stream)
+            _, ms = plan.build_profiled(x_dev, off, r, k, stream=stream)
             for s in STAGES:
                 stage_ms[s].append(ms[s])
     stage_avg = {s: float(np.mean(v[1:])) for s, v in stage_ms.items()}
     dom = max(stage_avg, key=stage_avg.get)
-    sbytes = stage_bytes(n_total, n_edges, D)
+    sbytes = stage_bytes(n_total, n_edges, d)
     hbm_peak, peak_kind = measured_peaks()
     achieved = sbytes[dom] / (stage_avg[dom] / 1e3) / 1e9
-    whole_bytes = 4 * n_total * D + 4 * (n_total + 1) + 4 * n_edges
+    whole_bytes = 4 * n_total * d + 4 * (n_total + 1) + 4 * n_edges
 
     # ---- e2e: host buffers in, host CSR out, through the C call
     e2e = None
@@ -404,16 +422,16 @@ def main(argv=None):
         import ctypes
         pinned_x = torch.from_numpy(x_host).pin_memory()
         out = dict(row_ptr=torch.zeros(n_total + 1, dtype=torch.int32).pin_memory().numpy(),
-                   col=torch.zeros(n_total * 64, dtype=torch.int32).pin_memory().numpy(),
+                   col=torch.zeros(n_total * epp, dtype=torch.int32).pin_memory().numpy(),
                    edge_off=np.zeros(B + 1, np.int32))
         xin = pinned_x.numpy()
-        plan.build_host(xin, off, R, K, out=out, stream=stream)
+        plan.build_host(xin, off, r, k, out=out, stream=stream)
         torch.cuda.synchronize(dev)
         e2e_steps = max(3, min(args.steps, 10))
         barrier(pg)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            plan.build_host(xin, off, R, K, out=out, stream=stream)
+            plan.build_host(xin, off, r, k, out=out, stream=stream)
         t1 = time.perf_counter()
         barrier(pg)
         e2e_s = max_over_ranks(pg, t1 - t0, dev)
@@ -427,13 +445,13 @@ def main(argv=None):
 
     # ---- served (continuous batching), rank 0 at N=1 only
     served = None
-    if rank == 0 and world == 1 and not args.no_served:
+    if rank == 0 and world == 1 and not args.no_served and args.workload == "c2":
         served = run_served(frnn, torch, args.served_requests)
 
     # ---- CPU oracle baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(x_host[off[0]:off[1]], args.cpu_queries)
+        cpu = run_cpu_baseline(x_host[off[0]:off[1]], args.cpu_queries, r=r, k=k)
 
     clocks = clk.summary()
     if rank == 0:
@@ -442,9 +460,13 @@ def main(argv=None):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": f"c2 batched: {B} events x N=120000 (seeded per event), D=8, r=0.1, K=256, "
-                            "one batched build per step replayed from a CUDA graph",
-                "events_per_step": B, "n_per_event": N_PER_EVENT, "d": D, "r": R, "k": K,
+                "workload": (f"{args.workload} batched: {B} events x "
+                             + (f"N={N_PER_EVENT}" if args.workload == "c2" else
+                                f"N in [{int(np.min(np.diff(off)))}, {n_max_event}]")
+                             + f" (seeded per event), D={d}, r={r}, K={k}, "
+                               "one batched build per step replayed from a CUDA graph"),
+                "events_per_step": B, "n_per_event": N_PER_EVENT if args.workload == "c2" else None,
+                "d": d, "r": r, "k": k, "autotune": tuned,
                 "points_per_step": n_total, "edges_per_step": n_edges,
                 "l2": f"inputs larger than L2 ({x_host.nbytes / 1e6:.0f} MB of points per step, "
                       f"plus {4 * n_edges / 1e6:.0f} MB of col written)",

@@ -126,6 +126,19 @@ FRNN_API int frnn_plan_set_tuning(frnn_plan* plan, const frnn_tuning* t);
 FRNN_API int frnn_plan_get_tuning(const frnn_plan* plan, frnn_tuning* t);
 
 /*
+ * Autotune the cell grid for a workload (the choice of gridded dimensions the
+ * paper makes by hand, Sec. 3.4): times the batched build of the given events
+ * for g_max in {4, 3, 2} x cell_scale in {1, 1.25, 1.5, 2} (best of three
+ * builds each, after one warm-up), sets the fastest on the plan, and returns
+ * it in *best and its time in *best_ms (either may be NULL).  Synchronous.
+ * Results never depend on the tuning, only the speed does.  Arguments and
+ * errors as frnn_build_graph_batched.
+ */
+FRNN_API int frnn_plan_autotune(frnn_plan* plan, const float* emb, const int64_t* ev_off, int n_events,
+                                int d, float r, int k_max, void* stream, frnn_tuning* best,
+                                float* best_ms);
+
+/*
  * Build the graph of one event (Sec. 2, Sec. 3.4; the cap of Sec. 3.1).
  *   emb    device, float32, row-major [n][d] with row stride d, caller-owned;
  *          it must stay unchanged until the stream reaches the end of the build.

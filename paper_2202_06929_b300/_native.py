@@ -32,7 +32,7 @@ ABI_FUNCTIONS = (
     "frnn_build_graph", "frnn_build_graph_batched", "frnn_build_graph_host", "frnn_build_graph_profiled",
     "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
-    "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy",
+    "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
 )
 
 
@@ -88,6 +88,8 @@ def load():
     lib.frnn_build_graph_profiled.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp,
                                               P(frnn_csr), P(ctypes.c_float), i32]
     lib.frnn_plan_bytes.argtypes = [P(frnn_plan_params), P(ctypes.c_uint64)]
+    lib.frnn_plan_autotune.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp, P(frnn_tuning),
+                                       P(ctypes.c_float)]
     lib.frnn_server_create.argtypes = [P(vp), P(frnn_server_params)]
     lib.frnn_server_reserved_bytes.argtypes = [vp, P(ctypes.c_uint64)]
     lib.frnn_server_submit.argtypes = [vp, vp, i64, P(ctypes.c_uint64)]
@@ -255,6 +257,18 @@ class Plan:
         t = frnn_tuning()
         _check(load().frnn_plan_get_tuning(self._h, ctypes.byref(t)), "frnn_plan_get_tuning")
         return int(t.g_max), float(t.cell_scale)
+
+    def autotune(self, emb, ev_off, r: float, k: int, stream=None) -> tuple[int, float, float]:
+        """frnn_plan_autotune on this batch: returns (g_max, cell_scale, ms) of
+        the fastest tuning, which stays set on the plan."""
+        ptr, n, d = self._emb_ptr(emb)
+        off = np.ascontiguousarray(ev_off, dtype=np.int64)
+        t = frnn_tuning()
+        ms = ctypes.c_float(0.0)
+        _check(load().frnn_plan_autotune(self._h, ptr, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         off.size - 1, d, float(r), int(k), _stream_handle(stream),
+                                         ctypes.byref(t), ctypes.byref(ms)), "frnn_plan_autotune")
+        return int(t.g_max), float(t.cell_scale), float(ms.value)
 
     def _emb_ptr(self, emb):
         torch = _torch()

@@ -494,6 +494,62 @@ int frnn_build_graph_profiled(frnn_plan* p, const float* emb, const int64_t* ev_
     return rc;
 }
 
+int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, float r,
+                       int k_max, void* stream, frnn_tuning* best, float* best_ms)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    static const int kG[] = {4, 3, 2};
+    static const float kScale[] = {1.0f, 1.25f, 1.5f, 2.0f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    const frnn_tuning saved = p->tuning;
+    frnn_tuning win = saved;
+    float win_ms = -1.f;
+    int rc = FRNN_OK;
+    frnn_csr out;
+    for (int gi = 0; gi < 3 && rc == FRNN_OK; ++gi) {
+        for (int si = 0; si < 4 && rc == FRNN_OK; ++si) {
+            p->tuning.g_max = kG[gi];
+            p->tuning.cell_scale = kScale[si];
+            rc = build_batched(p, emb, ev_off, n_events, d, r, k_max, s, &out);  // warm-up (and graph capture)
+            if (rc != FRNN_OK) break;
+            float best_rep = -1.f;
+            for (int rep = 0; rep < 3 && rc == FRNN_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = build_batched(p, emb, ev_off, n_events, d, r, k_max, s, &out);
+                cudaEventRecord(e1, s);
+                if (rc != FRNN_OK) break;
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = FRNN_ERR_CUDA;
+                    break;
+                }
+                if (best_rep < 0.f || ms < best_rep) best_rep = ms;
+            }
+            if (rc != FRNN_OK) break;
+            const int st = frnn_get_last_status(p, stream);
+            if (st == FRNN_OK && (win_ms < 0.f || best_rep < win_ms)) {
+                win_ms = best_rep;
+                win = p->tuning;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->tuning = (rc == FRNN_OK && win_ms >= 0.f) ? win : saved;
+    if (rc == FRNN_OK && win_ms < 0.f) rc = FRNN_ERR_CUDA;
+    if (best) *best = p->tuning;
+    if (best_ms) *best_ms = win_ms;
+    return rc;
+}
+
 int frnn_get_last_status(frnn_plan* p, void* stream)
 {
     if (!p) return FRNN_ERR_INVALID_ARG;
