@@ -338,10 +338,11 @@ def main(argv=None):
     stream = torch.cuda.Stream(device=dev)
     epp = k if args.workload == "c5b" else 64  # edge slots per point (C5b rows hold up to K)
 
+    cpp = 32  # cell slots per point: room for five or six gridded dims (the autotuner decides)
     plan = frnn.Plan(n_max=n_total, d_max=d, k_max_cap=k, events_max=B, edge_capacity=n_total * epp,
-                     use_graph=True, device=local)
+                     cells_per_point=cpp, use_graph=True, device=local)
     plan_one = frnn.Plan(n_max=n_max_event, d_max=d, k_max_cap=k, events_max=1,
-                         edge_capacity=n_max_event * epp, use_graph=True, device=local)
+                         edge_capacity=n_max_event * epp, cells_per_point=cpp, use_graph=True, device=local)
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()
@@ -351,7 +352,8 @@ def main(argv=None):
         tuned = {"batched": {"g_max": g, "cell_scale": scale, "build_ms": ms},
                  "plain": {"g_max": g1, "cell_scale": scale1, "build_ms": ms1},
                  "seconds": time.perf_counter() - t0,
-                 "searched": "g_max in {4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each"}
+                 "searched": "g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each",
+                 "cells_per_point": cpp}
 
     # ---- batched: the timed step
     with torch.cuda.stream(stream):

@@ -95,8 +95,10 @@ typedef struct {
 
 /*
  * Cell-grid tuning (speed only; the result never depends on it).
- * g_max: most hashed dimensions, 1..4 (0 = 4).  cell_scale: cell edge / r,
- * >= 1 (0 = 1).  The dimensions hashed are always the ones of widest extent.
+ * g_max: most gridded dimensions, 1..6 (0 = 4); a cell has 3^(g-1) runs of
+ * neighbouring cells, and a dimension is only gridded while the event's cell
+ * table (cells_per_point x n + 4096 slots) has room.  cell_scale: cell edge /
+ * r, >= 1 (0 = 1).  The dimensions gridded are always the ones of widest extent.
  */
 typedef struct {
     int g_max;
@@ -128,7 +130,7 @@ FRNN_API int frnn_plan_get_tuning(const frnn_plan* plan, frnn_tuning* t);
 /*
  * Autotune the cell grid for a workload (the choice of gridded dimensions the
  * paper makes by hand, Sec. 3.4): times the batched build of the given events
- * for g_max in {4, 3, 2} x cell_scale in {1, 1.25, 1.5, 2} (best of three
+ * for g_max in {6, 5, 4, 3, 2} x cell_scale in {1, 1.25, 1.5, 2} (best of three
  * builds each, after one warm-up), sets the fastest on the plan, and returns
  * it in *best and its time in *best_ms (either may be NULL).  Synchronous.
  * Results never depend on the tuning, only the speed does.  Arguments and

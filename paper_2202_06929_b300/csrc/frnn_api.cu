@@ -435,7 +435,7 @@ int frnn_plan_destroy(frnn_plan* p)
 int frnn_plan_set_tuning(frnn_plan* p, const frnn_tuning* t)
 {
     if (!p || !t) return FRNN_ERR_INVALID_ARG;
-    const int g = t->g_max == 0 ? 4 : t->g_max;
+    const int g = t->g_max == 0 ? 4 : t->g_max;  // default 4; up to kMaxG when the cell budget allows
     const float cs = t->cell_scale == 0.f ? 1.0f : t->cell_scale;
     if (g < 1 || g > kMaxG || !(cs >= 1.0f) || !std::isfinite(cs) || cs > 1e6f) return FRNN_ERR_INVALID_ARG;
     p->tuning.g_max = g;
@@ -501,7 +501,7 @@ int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, in
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    static const int kG[] = {4, 3, 2};
+    static const int kG[] = {6, 5, 4, 3, 2};
     static const float kScale[] = {1.0f, 1.25f, 1.5f, 2.0f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -514,7 +514,7 @@ int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, in
     float win_ms = -1.f;
     int rc = FRNN_OK;
     frnn_csr out;
-    for (int gi = 0; gi < 3 && rc == FRNN_OK; ++gi) {
+    for (int gi = 0; gi < 5 && rc == FRNN_OK; ++gi) {
         for (int si = 0; si < 4 && rc == FRNN_OK; ++si) {
             p->tuning.g_max = kG[gi];
             p->tuning.cell_scale = kScale[si];

@@ -5,7 +5,7 @@
 
 namespace frnn {
 
-constexpr int kMaxG = 4;            // most hashed (gridded) dimensions
+constexpr int kMaxG = 6;            // most gridded dimensions (3^(g-1) runs per cell)
 constexpr int kMaxDims = 64;        // largest embedding dimension
 constexpr int kChunk = 2048;        // points per chunk of the per-point kernels
 constexpr int kPtThreads = 256;     // threads of the per-point kernels

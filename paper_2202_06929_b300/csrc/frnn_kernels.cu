@@ -650,78 +650,58 @@ __device__ __forceinline__ void lane_event(const EvDesc* ev, int n_events, long 
     le.hi = le.pt_off + ev[le.b].n;
 }
 
-// The fields of an event's plan the walk needs, as scalars so that they stay
-// in registers (an indexed array here ended up in local memory).
-struct SegPlan {
-    int g, skip, cell_off;
-    int nc0, nc1, nc2, nc3;
-    int st0, st1, st2;       // strides of the slower dims (the fastest has stride 1)
-    int dm0, dm1, dm2, dm3;  // hashed embedding dims
-    float lo0, lo1, lo2, lo3;
-    float inv_s;
+// Per-warp shared-memory state of the walk: the current event's plan (copied
+// when the event changes; indexable without local memory), the cell
+// coordinates of the current segment, and a staging area for run compaction.
+struct WarpWalk {
+    EvPlan pl;
+    int ks[kMaxG];
+    int2 stage[32];
 };
 
-__device__ __forceinline__ void load_seg_plan(const EvPlan* plan, int b, SegPlan& sp)
+__device__ __forceinline__ void load_plan(WarpWalk& ww, const EvPlan* plan, int b, int lane)
 {
-    const EvPlan* p = plan + b;
-    sp.g = p->g;
-    sp.skip = p->skip;
-    sp.cell_off = p->cell_off;
-    sp.nc0 = p->ncell[0]; sp.nc1 = p->ncell[1]; sp.nc2 = p->ncell[2]; sp.nc3 = p->ncell[3];
-    sp.st0 = p->stride[0]; sp.st1 = p->stride[1]; sp.st2 = p->stride[2];
-    sp.dm0 = p->dims[0]; sp.dm1 = p->dims[1]; sp.dm2 = p->dims[2]; sp.dm3 = p->dims[3];
-    sp.lo0 = p->lo[0]; sp.lo1 = p->lo[1]; sp.lo2 = p->lo[2]; sp.lo3 = p->lo[3];
-    sp.inv_s = p->inv_s;
+    __syncwarp();
+    if (lane == 0) ww.pl = plan[b];
+    __syncwarp();
 }
 
-// Runs of the segment whose first query is staged at qrow[2 t + half].  Its
-// cell coordinates are recomputed from its coordinates with the operations
-// of cell_coord(), so they equal those the key kernel used.  Lane l < 3^(g-1)
-// takes one combination of offsets {-1,0,1} along the g-1 slower hashed dims;
-// along the fastest dim the three cells k-1..k+1 are adjacent in memory, so
-// each combination is one contiguous run of points.
-__device__ __forceinline__ void walk_runs(const SegPlan& pl, const float* qrow, int half,
-                                          const int* cell_start, int lane, int& beg, int& len)
+// Cell coordinates of the segment whose first query is staged at
+// qrow[2 t + half], recomputed with the operations of cell_coord(), so they
+// equal those the key kernel used.
+__device__ __forceinline__ void segment_cell(WarpWalk& ww, const float* qrow, int half, int lane)
 {
+    const EvPlan& pl = ww.pl;
+    if (lane < pl.g) ww.ks[lane] = cell_coord(qrow[2 * pl.dims[lane] + half], pl.lo[lane], pl.inv_s, pl.ncell[lane]);
+    __syncwarp();
+}
+
+// Run ri of the segment: ri < 3^(g-1) enumerates the offsets {-1,0,1} along
+// the g-1 slower gridded dims; along the fastest dim the cells k-1..k+1 are
+// adjacent in memory, so each combination is one contiguous run of points.
+__device__ __forceinline__ void run_of(const WarpWalk& ww, int ri, const int* cell_start, int& beg, int& len)
+{
+    const EvPlan& pl = ww.pl;
     const int g = pl.g;
-    const int k0 = cell_coord(qrow[2 * pl.dm0 + half], pl.lo0, pl.inv_s, pl.nc0);
-    const int k1 = g > 1 ? cell_coord(qrow[2 * pl.dm1 + half], pl.lo1, pl.inv_s, pl.nc1) : 0;
-    const int k2 = g > 2 ? cell_coord(qrow[2 * pl.dm2 + half], pl.lo2, pl.inv_s, pl.nc2) : 0;
-    const int k3 = g > 3 ? cell_coord(qrow[2 * pl.dm3 + half], pl.lo3, pl.inv_s, pl.nc3) : 0;
-    const int nr = g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
+    int rem = ri, cb = 0;
+    bool ok = true;
+#pragma unroll
+    for (int t = 0; t < kMaxG - 1; ++t) {
+        if (t < g - 1) {
+            const int kt = ww.ks[t] + (rem % 3) - 1;
+            rem /= 3;
+            ok &= (kt >= 0) && (kt < pl.ncell[t]);
+            cb += kt * pl.stride[t];
+        }
+    }
     beg = 0;
     len = 0;
-    if (lane < nr) {
-        const int o0 = lane % 3 - 1, o1 = (lane / 3) % 3 - 1, o2 = (lane / 9) % 3 - 1;
-        bool ok = true;
-        int cb = 0, kl = k0, ncl = pl.nc0;
-        if (g > 1) {
-            const int kt = k0 + o0;
-            ok &= (kt >= 0) && (kt < pl.nc0);
-            cb += kt * pl.st0;
-            kl = k1;
-            ncl = pl.nc1;
-        }
-        if (g > 2) {
-            const int kt = k1 + o1;
-            ok &= (kt >= 0) && (kt < pl.nc1);
-            cb += kt * pl.st1;
-            kl = k2;
-            ncl = pl.nc2;
-        }
-        if (g > 3) {
-            const int kt = k2 + o2;
-            ok &= (kt >= 0) && (kt < pl.nc2);
-            cb += kt * pl.st2;
-            kl = k3;
-            ncl = pl.nc3;
-        }
-        if (ok) {
-            const int c0 = cb + max(kl - 1, 0);
-            const int c1 = cb + min(kl + 1, ncl - 1);
-            beg = cell_start[pl.cell_off + c0];
-            len = cell_start[pl.cell_off + c1 + 1] - beg;
-        }
+    if (ok) {
+        const int kl = ww.ks[g - 1], ncl = pl.ncell[g - 1];
+        const int c0 = cb + max(kl - 1, 0);
+        const int c1 = cb + min(kl + 1, ncl - 1);
+        beg = cell_start[pl.cell_off + c0];
+        len = cell_start[pl.cell_off + c1 + 1] - beg;
     }
 }
 
@@ -738,21 +718,65 @@ __device__ __forceinline__ int find_run(int incl, int qi)
     return r;
 }
 
-// Candidate list of one segment: runs prefix-summed across the lanes.
+// A group of at most 32 runs, one per lane, prefix-summed across the lanes:
+// the candidates of the group are numbered 0 .. total-1 in run order.
 struct Runs {
     int beg, incl, excl, total;
 };
 
-__device__ __forceinline__ Runs segment_runs(const SegPlan& pl, const float* qrow, int half,
-                                             const int* cell_start, int lane)
+__device__ __forceinline__ Runs make_runs(int beg, int len, int lane)
 {
     Runs r;
-    int len;
-    walk_runs(pl, qrow, half, cell_start, lane, r.beg, len);
+    r.beg = beg;
     r.incl = warp_incl_scan(len, lane);
     r.excl = r.incl - len;
     r.total = __shfl_sync(kFull, r.incl, 31);
     return r;
+}
+
+__device__ __forceinline__ int n_runs(int g)
+{
+    return g >= 6 ? 243 : g == 5 ? 81 : g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
+}
+
+// Calls body(Runs) for the segment's runs, in groups of at most 32.  With at
+// most 32 runs (g <= 4) the runs go to the lanes as they are; with more,
+// they are generated 32 at a time and only the non-empty ones are packed
+// into the lanes (at g = 5 or 6 most of the 81 or 243 runs are empty).
+template <typename Body>
+__device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int* cell_start, int lane, Body&& body)
+{
+    const int nr = n_runs(ww.pl.g);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (nr <= 32) {
+        int beg = 0, len = 0;
+        if (lane < nr) run_of(ww, lane, cell_start, beg, len);
+        if (__ballot_sync(kFull, len > 0)) body(make_runs(beg, len, lane));
+        return;
+    }
+    int cnt = 0, gbeg = 0, glen = 0;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        int beg = 0, len = 0;
+        if (r0 + lane < nr) run_of(ww, r0 + lane, cell_start, beg, len);
+        const unsigned m = __ballot_sync(kFull, len > 0);
+        const int nne = __popc(m);
+        if (cnt + nne > 32) {
+            body(make_runs(gbeg, glen, lane));
+            cnt = 0;
+            gbeg = 0;
+            glen = 0;
+        }
+        if (len > 0) ww.stage[cnt + __popc(m & lt_mask)] = make_int2(beg, len);
+        __syncwarp();
+        if (lane >= cnt && lane < cnt + nne) {
+            const int2 v = ww.stage[lane];
+            gbeg = v.x;
+            glen = v.y;
+        }
+        __syncwarp();
+        cnt += nne;
+    }
+    if (cnt > 0) body(make_runs(gbeg, glen, lane));
 }
 
 // Sorted position of candidate number qi of the segment (or -1 past the end).
@@ -844,7 +868,7 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
 // Rows with |S_i| <= kFast are kept whole by the collect walk (one 32-key
 // slot per query in shared memory) and sorted there; longer rows are left to
 // the emit walk, which selects the k smallest keys on its own.
-constexpr int kFast = 32;
+constexpr int kFast = 24;
 constexpr int kRowSlots = kFast + 1;   // a row also holds the query's own key while collecting
 constexpr int kRowStride = kFast + 1;  // = kRowSlots; odd, so row starts of lanes 0..15 fall in distinct banks
 
@@ -881,8 +905,9 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     LaneEvent le;
     le.lo = 1;
     le.hi = 0;
+    __shared__ WarpWalk s_ww[kWalkThreads / 32];
+    WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    SegPlan pl;
     for (long long ch = (long long)blockIdx.x * (kWalkThreads / 32) + wib; ch < nchunks; ch += nwarps) {
         const long long q0 = ch << 5;
         const long long q = q0 + lane;
@@ -898,12 +923,13 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
             const int e = seg ? __ffs(seg) - 1 : nvalid;
             const int sb = __shfl_sync(kFull, le.b, a);
             if (sb != plan_b) {
-                load_seg_plan(st.plan, sb, pl);
+                load_plan(ww, st.plan, sb, lane);
                 plan_b = sb;
             }
-            if (pl.skip) continue;
-            const Runs rn = segment_runs(pl, sq + (a >> 1) * (2 * DP), a & 1, st.cell_start, lane);
+            if (ww.pl.skip) continue;
+            segment_cell(ww, sq + (a >> 1) * (2 * DP), a & 1, lane);
             const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
+            for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
                 CandPk<DP4> cp;
@@ -930,6 +956,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
                     }
                 }
             }
+            });
         }
         // pool space for the chunk's short rows
         const int raw = deg;                 // includes the query itself
@@ -1013,8 +1040,9 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     LaneEvent le;
     le.lo = 1;
     le.hi = 0;
+    __shared__ WarpWalk s_ww[kFillThreads / 32];
+    WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    SegPlan pl;
     for (long long ch = (long long)blockIdx.x * (kFillThreads / 32) + wib; ch < nchunks; ch += nwarps) {
         const long long q0 = ch << 5;
         const long long q = q0 + lane;
@@ -1062,14 +1090,15 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
             const int rsi = __shfl_sync(kFull, rs, i);
             const int cnti = __shfl_sync(kFull, cnt, i);
             if (sb != plan_b) {
-                load_seg_plan(st.plan, sb, pl);
+                load_plan(ww, st.plan, sb, lane);
                 plan_b = sb;
             }
             const float* qrow = sq + (i >> 1) * (2 * DP);
             const int half = i & 1;
-            const Runs rn = segment_runs(pl, qrow, half, st.cell_start, lane);
+            segment_cell(ww, qrow, half, lane);
             unsigned long long thr = ~0ull;
             int nk = 0;
+            for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
                 unsigned long long key = ~0ull;
@@ -1095,6 +1124,7 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
                 nk += __popc(m);
                 __syncwarp();
             }
+            });
             const int nout = min(cnti, nk);
             if (nk <= 32) {
                 unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;

@@ -225,7 +225,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     h.k = k_max;
     h.r = r;
     h.r2 = r * r;
-    h.g_max = kMaxG;
+    h.g_max = 4;
     h.cell_scale = 1.0f;
     h.emit_d2 = 0;
     h.edge_capacity = col_capacity < cap_edges ? col_capacity : cap_edges;

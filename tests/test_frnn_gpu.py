@@ -17,13 +17,13 @@ pytestmark = pytest.mark.gpu
 import paper_2202_06929_b300 as frnn  # noqa: E402
 
 
-def gpu_csr(x, r, k, emit_d2=False, use_graph=False, tuning=None, plan=None):
+def gpu_csr(x, r, k, emit_d2=False, use_graph=False, tuning=None, plan=None, cells_per_point=0):
     x = np.ascontiguousarray(x, dtype=np.float32)
     n, d = x.shape
     own = plan is None
     if own:
         plan = frnn.Plan(n_max=max(n, 1), d_max=d, k_max_cap=max(k, 1), emit_d2=emit_d2,
-                         use_graph=use_graph)
+                         use_graph=use_graph, cells_per_point=cells_per_point)
     try:
         if tuning:
             plan.set_tuning(*tuning)
@@ -104,10 +104,17 @@ def test_property_sweep(case, n, d, k, kind, r):
     assert_same_as_oracle(x, r, k)
 
 
-@pytest.mark.parametrize("g_max,scale", [(1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0), (4, 1.5), (3, 2.0), (2, 3.7)])
+@pytest.mark.parametrize("g_max,scale", [(1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0), (4, 1.5), (3, 2.0), (2, 3.7),
+                                         (5, 1.0), (6, 1.0), (6, 1.5), (5, 2.0)])
 def test_tuning_never_changes_result(g_max, scale):
+    # a cell budget large enough for five and six gridded dims (81 and 243 runs per cell)
     x = synth.clustered_grid(4000, 8, 5, 300, 0.03, 0.15)
-    assert_same_as_oracle(x, 0.1, 16, tuning=(g_max, scale))
+    assert_same_as_oracle(x, 0.1, 16, tuning=(g_max, scale), cells_per_point=512)
+
+
+def test_six_gridded_dims_high_dimensional_event():
+    x = synth.clustered_grid(20000, 12, 8, 1500, 0.03, 0.25)
+    assert_same_as_oracle(x, 0.15, 40, tuning=(6, 1.0), cells_per_point=256)
 
 
 # ------------------------------------------------------------------ edge cases
