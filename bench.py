@@ -404,6 +404,26 @@ def main(argv=None):
         raise RuntimeError(f"plain status: {frnn.status_string(st)}")
     plain_value = B / (plain_wall / 1e3)
 
+    # ---- track labeling (connected components of the built graph, every edge kept)
+    labeling = None
+    with torch.cuda.stream(stream):
+        plan.build_batched(x_dev, off, r, k, stream=stream)
+        lab = torch.empty(n_total, dtype=torch.int32, device=dev)
+        plan.label_components(float("inf"), stream=stream, out=lab)
+        le0, le1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lab_ms = []
+        for _ in range(5):
+            le0.record(stream)
+            plan.label_components(float("inf"), stream=stream, out=lab)
+            le1.record(stream)
+            le1.synchronize()
+            lab_ms.append(le0.elapsed_time(le1))
+    if plan.last_status(stream) == 0:
+        n_tracks = int((lab.cpu().numpy() == np.arange(n_total) - np.repeat(off[:-1], np.diff(off))).sum())
+        labeling = {"ms_per_step": float(np.median(lab_ms)), "components_per_step": n_tracks,
+                    "note": "frnn_label_components: weakly connected components of the step's graphs "
+                            "(all edges kept), 3 kernels, after the build on the same stream"}
+
     # ---- per-stage times of the batched build (CUDA events between stages)
     stage_ms = {s: [] for s in STAGES}
     with torch.cuda.stream(stream):
@@ -506,6 +526,7 @@ def main(argv=None):
                                          "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
                                          "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak}},
             "e2e": e2e,
+            "labeling": labeling,
             "served": served,
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_BUILD * args.steps,

@@ -198,6 +198,22 @@ FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const 
                                        frnn_csr* out, float* stage_ms, int n_stages);
 
 /*
+ * Track labeling on the plan's last build (the step after graph building,
+ * Sec. 2: edges passing a score cut grouped into weakly connected
+ * components, each a track candidate; Sec. 3.2 uses cuGraph's WCC).  The
+ * score here is the edge's d2: edges with d2 <= d2_max are kept, their
+ * direction is ignored, and labels[p] (device int32, one per point of the
+ * last call) receives the smallest event-local index of p's component.
+ * d2_max >= r*r keeps every edge; a smaller cut needs a plan created with
+ * FRNN_EMIT_D2.  Asynchronous on `stream` (enqueue it after the build on the
+ * same stream); uses the plan's scratch, so it must run before the next
+ * build.  Call it only after a build without OVERFLOW.  Errors: INVALID_ARG
+ * (NULL, no build yet, NaN cut, cut below r*r without FRNN_EMIT_D2), CUDA;
+ * a bounded retry that ran out latches FRNN_ERR_TIMEOUT.
+ */
+FRNN_API int frnn_label_components(frnn_plan* plan, float d2_max, void* stream, int32_t* labels);
+
+/*
  * Synchronise `stream`, then return and clear the status latched by the
  * plan's kernels since the last call (FRNN_OK if none).  If several errors
  * were latched the most severe is returned, in the order TIMEOUT, OVERFLOW,

@@ -52,6 +52,8 @@ def _configure(lib):
     lib.fo_fill_grid.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                  ctypes.c_int, _i64p, ctypes.c_int64, _i64p, _i32p, _i64p]
     lib.fo_num_threads.argtypes = []
+    lib.fo_components.argtypes = [_i64p, _i32p, _f32p, ctypes.c_float, ctypes.c_int64, _i32p]
+    lib.fo_components.restype = ctypes.c_int
     for f in (lib.fo_degree, lib.fo_fill, lib.fo_degree_grid, lib.fo_fill_grid, lib.fo_num_threads):
         f.restype = ctypes.c_int
     return lib
@@ -167,3 +169,25 @@ def radius_graph_grid(m: np.ndarray, thr: int, k: int, queries=None, with_q: boo
     if with_q:
         return row_ptr, col[:e], qv[:e]
     return row_ptr, col[:e]
+
+
+def components(row_ptr: np.ndarray, col: np.ndarray, w=None, w_max: float = float("inf")) -> np.ndarray:
+    """Weakly connected components of a CSR graph (edges with w <= w_max,
+    direction ignored): each point's label is the smallest index of its
+    component.  Paper: Sec. 2 (track candidates from a score cut and weakly
+    connected components), Sec. 3.2."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    wt = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    n = rp.size - 1
+    labels = np.zeros(max(n, 1), dtype=np.int32)
+    if n and _load().fo_components(_ptr(rp, _i64p), _ptr(c, _i32p), _ptr(wt, _f32p), float(w_max), n,
+                                   _ptr(labels, _i32p)) != 0:
+        raise ValueError("oracle: bad argument")
+    return labels[:n]
+
+
+def track_labels(x: np.ndarray, r: float, k: int, d2_max: float) -> np.ndarray:
+    """Labels of the capped radius graph's edges with d2 <= fl32(d2_max)."""
+    rp, col, d2 = radius_graph(x, r, k, with_d2=True)
+    return components(rp, col, d2, float(np.float32(d2_max)))

@@ -24,6 +24,12 @@
  * (q, j).  With thr = floor(r2 * 65536) it gives the same graph as the float
  * path on grid inputs, through arithmetic that shares nothing with it.
  *
+ * Track labeling (the step after graph building, Sec. 2: edges that pass a
+ * score cut are grouped into weakly connected components, each one a track
+ * candidate; Sec. 3.2): fo_components treats every edge i -> j of a CSR
+ * whose weight is <= w_max as undirected and labels each point with the
+ * smallest point index of its component (sequential union-find).
+ *
  * Plain brute force, O(n^2 d) per pass, parallel over queries with OpenMP.
  * Every function returns 0 on success and -1 on a bad argument or a failed
  * allocation.
@@ -258,4 +264,39 @@ int fo_num_threads(void)
         }
     }
     return t;
+}
+
+static int64_t fo_find(int64_t* parent, int64_t x)
+{
+    while (parent[x] != x) x = parent[x];
+    return x;
+}
+
+/*
+ * Weakly connected components of the graph whose edges are the CSR entries
+ * (row i, col[e]) with w[e] <= w_max (w == NULL keeps every edge).  labels[i]
+ * receives the smallest index of i's component.  Sequential union-find: the
+ * larger root is attached under the smaller, so every root is the minimum of
+ * its component.
+ */
+int fo_components(const int64_t* row_ptr, const int32_t* col, const float* w, float w_max, int64_t n,
+                  int32_t* labels)
+{
+    if (n < 0 || (n > 0 && (!row_ptr || !labels))) return -1;
+    int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!parent) return -1;
+    for (int64_t i = 0; i < n; ++i) parent[i] = i;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (w && !(w[e] <= w_max)) continue;
+            int64_t j = col[e];
+            if (j < 0 || j >= n) { free(parent); return -1; }
+            int64_t a = fo_find(parent, i), b = fo_find(parent, j);
+            if (a == b) continue;
+            if (a < b) parent[b] = a; else parent[a] = b;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) labels[i] = (int32_t)fo_find(parent, i);
+    free(parent);
+    return 0;
 }

@@ -33,6 +33,7 @@ ABI_FUNCTIONS = (
     "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
+    "frnn_label_components",
 )
 
 
@@ -98,6 +99,7 @@ def load():
                                           P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double)]
     lib.frnn_server_destroy.argtypes = [vp]
     lib.frnn_build_graph_noalloc.argtypes = [vp, i64, i32, f32, i32, vp, vp, i64, vp, vp]
+    lib.frnn_label_components.argtypes = [vp, f32, vp, vp]
     lib.frnn_get_last_status.argtypes = [vp, vp]
     lib.frnn_status_string.argtypes = [i32]
     lib.frnn_status_string.restype = ctypes.c_char_p
@@ -227,6 +229,7 @@ class Plan:
         self.device = _torch().device("cuda", device)
         self.params = prm
         self.edge_capacity = int(edge_capacity) if edge_capacity else int(n_max) * int(k_max_cap)
+        self._last_n = 0
 
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:
@@ -282,6 +285,7 @@ class Plan:
         c = frnn_csr()
         _check(load().frnn_build_graph(self._h, ptr, n, d, float(r), int(k), _stream_handle(stream),
                                        ctypes.byref(c)), "frnn_build_graph")
+        self._last_n = n
         return Csr(c, self.device, np.array([0, n], dtype=np.int64), self.edge_capacity)
 
     def build_batched(self, emb, ev_off, r: float, k: int, stream=None) -> Csr:
@@ -293,6 +297,7 @@ class Plan:
         _check(load().frnn_build_graph_batched(self._h, ptr, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                                off.size - 1, d, float(r), int(k), _stream_handle(stream),
                                                ctypes.byref(c)), "frnn_build_graph_batched")
+        self._last_n = n
         return Csr(c, self.device, off, self.edge_capacity)
 
     STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
@@ -329,6 +334,17 @@ class Plan:
         out["n_edges"] = int(ne.value)
         _check(rc, "frnn_build_graph_host")
         return out
+
+    def label_components(self, d2_max: float = float("inf"), stream=None, out=None):
+        """frnn_label_components on the last build: event-local component
+        labels (smallest index of each point's component), as an int32 CUDA
+        tensor with one entry per point of the last call."""
+        torch = _torch()
+        n = int(self._last_n)
+        labels = out if out is not None else torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        _check(load().frnn_label_components(self._h, float(min(d2_max, 3.0e38)), _stream_handle(stream),
+                                            labels.data_ptr()), "frnn_label_components")
+        return labels[:n]
 
     def last_status(self, stream=None) -> int:
         """frnn_get_last_status: synchronise and return (and clear) the device status."""

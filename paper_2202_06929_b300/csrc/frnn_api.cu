@@ -77,6 +77,8 @@ struct frnn_plan {
     float* d_input = nullptr;
     long long d_input_floats = 0;
     frnn_csr last{};
+    float last_r2 = 0.f;
+    bool has_last = false;
 };
 
 namespace {
@@ -223,6 +225,8 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
             cudaMemsetAsync(st.edge_off, 0, sizeof(int) * (n_events + 1), s) != cudaSuccess)
             return FRNN_ERR_CUDA;
         p->last = *out;
+        p->last_r2 = r * r;
+        p->has_last = true;
         return FRNN_OK;
     }
     // stage the per-call header and event table
@@ -265,6 +269,8 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     rc = launch(p, h->dp / 4, cap, s, stage_ev);
     if (rc != FRNN_OK) return rc;
     p->last = *out;
+    p->last_r2 = r * r;
+    p->has_last = true;
     return FRNN_OK;
 }
 
@@ -548,6 +554,20 @@ int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, in
     if (best) *best = p->tuning;
     if (best_ms) *best_ms = win_ms;
     return rc;
+}
+
+int frnn_label_components(frnn_plan* p, float d2_max, void* stream, int32_t* labels)
+{
+    if (!p || !labels || std::isnan(d2_max)) return FRNN_ERR_INVALID_ARG;
+    if (!p->has_last) return FRNN_ERR_INVALID_ARG;
+    const bool all = d2_max >= p->last_r2;
+    if (!all && !(p->prm.flags & FRNN_EMIT_D2)) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    if (p->last.n_total == 0) return FRNN_OK;
+    const int grid = p->n_sm * 8;
+    return launch_label(p->st, reinterpret_cast<int*>(p->st.key), labels, d2_max, all ? 0 : 1, grid, stream) == 0
+               ? FRNN_OK : FRNN_ERR_CUDA;
 }
 
 int frnn_get_last_status(frnn_plan* p, void* stream)

@@ -113,6 +113,9 @@ struct LaunchCfg {
 constexpr int kStages = 7;
 int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream, void* stage_events);
 int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg);
+// Weakly connected components of the last build (frnn_label.cu); parent is
+// n_total ints of scratch, labels receives event-local component labels.
+int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int use_d2, int grid, void* stream);
 int config_pt(int n_sm, LaunchCfg* cfg);
 
 }  // namespace frnn

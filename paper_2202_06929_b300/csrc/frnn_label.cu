@@ -1,0 +1,126 @@
+// Track labeling over a built graph: weakly connected components.
+//
+// The step after graph building in the paper's pipeline (Sec. 2): edges that
+// pass a score cut are grouped into weakly connected components, each one a
+// track candidate; the paper runs cuGraph's lock-free WCC on the GPU
+// (Sec. 3.2).  Here the score of an edge is its squared distance (no trained
+// network is involved): an edge i -> j is kept when d2 <= d2_max, its
+// direction is ignored, and every point gets the smallest index of its
+// component as its label, so labels are unique and independent of timing.
+//
+// Lock-free union-find over a parent array of call-wide point indices: a root
+// is only ever attached (by compare-and-swap) under a smaller root, and path
+// halving only moves a pointer to an ancestor, so every parent pointer is <=
+// its index; finds therefore end after at most `index` steps, and the root of
+// a component is its minimum.
+#include <cuda_runtime.h>
+
+#include "frnn_internal.h"
+
+namespace frnn {
+namespace {
+
+constexpr int kLabelThreads = 256;
+constexpr int kUnionLimit = 1 << 20;  // retries of one union (each failure means another thread progressed)
+
+__device__ __forceinline__ int ld_volatile(const int* p)
+{
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+__device__ __forceinline__ int find_root(int* parent, int x)
+{
+    for (;;) {
+        const int px = ld_volatile(parent + x);
+        if (px == x) return x;
+        const int ppx = ld_volatile(parent + px);
+        if (ppx != px) parent[x] = ppx;  // path halving: ppx is an ancestor of x
+        x = ppx;
+    }
+}
+
+__device__ __forceinline__ bool unite(int* parent, int a, int b)
+{
+    for (int it = 0; it < kUnionLimit; ++it) {
+        a = find_root(parent, a);
+        b = find_root(parent, b);
+        if (a == b) return true;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(parent + b, b, a);  // attach the larger root under the smaller
+        if (old == b) return true;
+        b = old;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int event_of(const EvDesc* ev, int n_events, long long p)
+{
+    int lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ev[mid].pt_off <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* parent)
+{
+    const long long P = st.hdr->n_total;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
+        parent[p] = (int)p;
+}
+
+__global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int* parent, float d2_max, int use_d2)
+{
+    const long long P = st.hdr->n_total;
+    const int B = st.hdr->n_events;
+    const long long ecap = st.hdr->edge_capacity;
+    long long lo = 1, hi = 0, off = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        if (p < lo || p >= hi) {
+            const int b = event_of(st.ev, B, p);
+            off = st.ev[b].pt_off;
+            lo = off;
+            hi = off + st.ev[b].n;
+        }
+        const int rs = st.row_ptr[p], re = st.row_ptr[p + 1];
+        if ((long long)re > ecap) continue;  // rows past the edge capacity were never written
+        for (int e = rs; e < re; ++e) {
+            if (use_d2 && !(st.d2[e] <= d2_max)) continue;
+            if (!unite(parent, (int)p, (int)(off + st.col[e]))) atomicOr(st.status, kStTimeout);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLabelThreads) k_label_final(DevState st, int* parent, int* labels)
+{
+    const long long P = st.hdr->n_total;
+    const int B = st.hdr->n_events;
+    long long lo = 1, hi = 0, off = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        if (p < lo || p >= hi) {
+            const int b = event_of(st.ev, B, p);
+            off = st.ev[b].pt_off;
+            lo = off;
+            hi = off + st.ev[b].n;
+        }
+        labels[p] = (int)(find_root(parent, (int)p) - off);
+    }
+}
+
+}  // namespace
+
+int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int use_d2, int grid, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_label_init<<<grid, kLabelThreads, 0, s>>>(st, parent);
+    k_label_union<<<grid, kLabelThreads, 0, s>>>(st, parent, d2_max, use_d2);
+    k_label_final<<<grid, kLabelThreads, 0, s>>>(st, parent, labels);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace frnn

@@ -326,3 +326,39 @@ def test_pins_reject_planted_mistake(mutant):
 
 def test_pins_pass_on_the_real_oracle():
     assert _pins_pass()
+
+
+# --------------------------------------------------------------------------- track labeling
+
+def test_components_closed_forms():
+    # a chain 0-1-2-3 given by one directed edge per link, and two isolated points
+    rp = np.array([0, 1, 2, 3, 3, 3, 3])
+    col = np.array([1, 2, 3], np.int32)
+    assert oracle.components(rp, col).tolist() == [0, 0, 0, 0, 4, 5]
+    # the same links pointing the other way: weak connectivity ignores direction
+    rp = np.array([0, 0, 1, 2, 3, 3, 3])
+    col = np.array([0, 1, 2], np.int32)
+    assert oracle.components(rp, col).tolist() == [0, 0, 0, 0, 4, 5]
+    # a weight cut splits the chain
+    w = np.array([0.1, 0.9, 0.1], np.float32)
+    assert oracle.components(rp, col, w, 0.5).tolist() == [0, 0, 2, 2, 4, 5]
+
+
+@pytest.mark.parametrize("cut", [1.0, 0.5, 0.2])
+def test_components_equal_networkx(cut):
+    import networkx as nx
+    x = synth.clustered_grid(2500, 8, 41, 120, 0.03, 0.2)
+    r, k = 0.1, 8
+    rp, col, d2 = oracle.radius_graph(x, r, k, with_d2=True)
+    d2_max = float(np.float32(cut * cut * r * r))
+    labels = oracle.components(rp, col, d2, d2_max)
+    g = nx.Graph()
+    g.add_nodes_from(range(x.shape[0]))
+    for i in range(x.shape[0]):
+        for e in range(rp[i], rp[i + 1]):
+            if d2[e] <= np.float32(d2_max):
+                g.add_edge(i, int(col[e]))
+    want = np.empty(x.shape[0], np.int32)
+    for comp in nx.connected_components(g):
+        want[list(comp)] = min(comp)
+    np.testing.assert_array_equal(labels, want)
