@@ -58,6 +58,12 @@ typedef enum {
     FRNN_ERR_CAPACITY = 7         /* the call exceeds a capacity fixed at plan creation */
 } frnn_status;
 
+/* k_max value that keeps every row whole: the paper's own FRNN list (Sec. 3.4,
+ * all points within r, unsorted).  Rows of at most 24 neighbours still come
+ * sorted by (d2, j); longer rows are in no particular order.  The edges must
+ * fit the plan's edge capacity (FRNN_ERR_OVERFLOW otherwise). */
+#define FRNN_NO_CAP 0
+
 /* Plan flags. */
 #define FRNN_EMIT_D2 0x1u    /* also write the float32 d2 of every edge              */
 #define FRNN_USE_GRAPH 0x2u  /* replay the build as a CUDA graph captured on first use */
@@ -145,7 +151,8 @@ FRNN_API int frnn_plan_autotune(frnn_plan* plan, const float* emb, const int64_t
  *   emb    device, float32, row-major [n][d] with row stride d, caller-owned;
  *          it must stay unchanged until the stream reaches the end of the build.
  *   n      points, 0 <= n <= n_max.       d  dimension, 1 <= d <= d_max.
- *   r      radius, finite and > 0.        k_max  cap, 1 <= k_max <= k_max_cap.
+ *   r      radius, finite and > 0.        k_max  cap, 1 <= k_max <= k_max_cap,
+ *          or FRNN_NO_CAP.
  *   stream cudaStream_t the work is enqueued on (asynchronous; no host sync).
  *   out    receives the plan-owned device pointers (n_events = 1).
  * Errors: INVALID_ARG (NULL plan/out, NULL emb with n > 0, sizes out of range,
@@ -212,6 +219,21 @@ FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const 
  * a bounded retry that ran out latches FRNN_ERR_TIMEOUT.
  */
 FRNN_API int frnn_label_components(frnn_plan* plan, float d2_max, void* stream, int32_t* labels);
+
+/*
+ * Edge features for the filter stage (Sec. 3: the edge-filter network reads
+ * the graph's edges in fixed-size batches, 800k edges in the paper): for the
+ * edges e_begin .. e_end-1 of the plan's last build (CSR order, call-wide
+ * edge numbers as in frnn_csr), out[(e - e_begin) * (2d + 1) + ...] receives
+ * x_i[0..d), x_j[0..d) and d2(i, j) (the same float32 value the build
+ * tested).  emb: device float32 [n_total][d], the points of the last build.
+ * out: device float32 [(e_end - e_begin) * (2d + 1)].  Asynchronous; call
+ * after the build on the same stream, before the next build.  Errors:
+ * INVALID_ARG (NULL, no build yet, bad range or e_end beyond the edge
+ * capacity), CUDA.
+ */
+FRNN_API int frnn_edge_features(frnn_plan* plan, const float* emb, int64_t e_begin, int64_t e_end, float* out,
+                                void* stream);
 
 /*
  * Synchronise `stream`, then return and clear the status latched by the

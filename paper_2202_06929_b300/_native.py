@@ -23,6 +23,7 @@ FRNN_ERR_TIMEOUT = 5
 FRNN_ERR_OVERFLOW = 6
 FRNN_ERR_CAPACITY = 7
 
+FRNN_NO_CAP = 0   # k = FRNN_NO_CAP keeps every row whole (rows over 24 neighbours unsorted)
 FRNN_EMIT_D2 = 0x1
 FRNN_USE_GRAPH = 0x2
 
@@ -33,7 +34,7 @@ ABI_FUNCTIONS = (
     "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
-    "frnn_label_components",
+    "frnn_label_components", "frnn_edge_features",
 )
 
 
@@ -100,6 +101,7 @@ def load():
     lib.frnn_server_destroy.argtypes = [vp]
     lib.frnn_build_graph_noalloc.argtypes = [vp, i64, i32, f32, i32, vp, vp, i64, vp, vp]
     lib.frnn_label_components.argtypes = [vp, f32, vp, vp]
+    lib.frnn_edge_features.argtypes = [vp, vp, i64, i64, vp, vp]
     lib.frnn_get_last_status.argtypes = [vp, vp]
     lib.frnn_status_string.argtypes = [i32]
     lib.frnn_status_string.restype = ctypes.c_char_p
@@ -345,6 +347,19 @@ class Plan:
         _check(load().frnn_label_components(self._h, float(min(d2_max, 3.0e38)), _stream_handle(stream),
                                             labels.data_ptr()), "frnn_label_components")
         return labels[:n]
+
+    def edge_features(self, emb, e_begin: int, e_end: int, stream=None, out=None):
+        """frnn_edge_features: [x_i, x_j, d2] rows for edges [e_begin, e_end) of
+        the last build (emb: the points of that build), as a CUDA tensor of
+        shape [e_end - e_begin, 2d + 1]."""
+        torch = _torch()
+        ptr, n, d = self._emb_ptr(emb)
+        m = max(int(e_end) - int(e_begin), 0)
+        if out is None:
+            out = torch.empty((max(m, 1), 2 * d + 1), dtype=torch.float32, device=self.device)
+        _check(load().frnn_edge_features(self._h, ptr, int(e_begin), int(e_end), out.data_ptr(),
+                                         _stream_handle(stream)), "frnn_edge_features")
+        return out[:m]
 
     def last_status(self, stream=None) -> int:
         """frnn_get_last_status: synchronise and return (and clear) the device status."""

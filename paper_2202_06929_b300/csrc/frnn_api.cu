@@ -190,14 +190,14 @@ int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off
                      int d, float r, int k, frnn_csr* out, long long* n_total)
 {
     if (!p || !out || !ev_off) return FRNN_ERR_INVALID_ARG;
-    if (n_events < 1 || d < 1 || d > kMaxDims || k < 1 || k > 1024) return FRNN_ERR_INVALID_ARG;
+    if (n_events < 1 || d < 1 || d > kMaxDims || k < 0 || k > 1024) return FRNN_ERR_INVALID_ARG;
     if (!(r > 0.0f) || !std::isfinite(r)) return FRNN_ERR_INVALID_ARG;
     if (ev_off[0] != 0) return FRNN_ERR_INVALID_ARG;
     for (int b = 0; b < n_events; ++b)
         if (ev_off[b + 1] < ev_off[b]) return FRNN_ERR_INVALID_ARG;
     const long long n = ev_off[n_events];
     if (n > 0 && (!emb || (reinterpret_cast<uintptr_t>(emb) & 3u))) return FRNN_ERR_INVALID_ARG;
-    if (n * (long long)k >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;
+    if (n * (long long)k >= (1ll << 31)) return FRNN_ERR_INVALID_ARG;  // k = 0 (no cap): bounded by the edge capacity
     if (n_events > p->prm.events_max || n > p->prm.n_max || d > p->prm.d_max || k > p->prm.k_max_cap)
         return FRNN_ERR_CAPACITY;
     float r2 = r * r;
@@ -254,7 +254,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->total_chunks = chunks;
     h->d = d;
     h->dp = (d + 3) & ~3;
-    h->k = k;
+    h->k = (k == FRNN_NO_CAP) ? 0x7fffffff : k;
     h->r = r;
     h->r2 = r * r;
     h->g_max = p->tuning.g_max;
@@ -568,6 +568,17 @@ int frnn_label_components(frnn_plan* p, float d2_max, void* stream, int32_t* lab
     const int grid = p->n_sm * 8;
     return launch_label(p->st, reinterpret_cast<int*>(p->st.key), labels, d2_max, all ? 0 : 1, grid, stream) == 0
                ? FRNN_OK : FRNN_ERR_CUDA;
+}
+
+int frnn_edge_features(frnn_plan* p, const float* emb, int64_t e_begin, int64_t e_end, float* out, void* stream)
+{
+    if (!p || !p->has_last || e_begin < 0 || e_end < e_begin) return FRNN_ERR_INVALID_ARG;
+    if (e_end > e_begin && (!emb || !out)) return FRNN_ERR_INVALID_ARG;
+    if (e_end > p->edge_cap) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    if (e_end == e_begin || p->last.n_total == 0) return FRNN_OK;
+    return launch_edge_features(p->st, emb, e_begin, e_end, out, p->n_sm * 8, stream) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
 }
 
 int frnn_get_last_status(frnn_plan* p, void* stream)

@@ -1096,6 +1096,29 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
             const float* qrow = sq + (i >> 1) * (2 * DP);
             const int half = i & 1;
             segment_cell(ww, qrow, half, lane);
+            if (K == 0x7fffffff) {
+                // no cap: the whole row, written in candidate order
+                int nw = 0;
+                for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    float d2 = 0.f;
+                    bool take = false;
+                    if (cand >= 0) {
+                        d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
+                        take = d2 <= r2 && (long long)cand != q0 + i;
+                    }
+                    const unsigned m = __ballot_sync(kFull, take);
+                    const int slot = nw + __popc(m & lt_mask);
+                    if (take && slot < cnti) {
+                        st.col[rsi + slot] = __ldg(st.perm + cand);
+                        if (emit) st.d2[rsi + slot] = d2;
+                    }
+                    nw += __popc(m);
+                }
+                });
+                continue;
+            }
             unsigned long long thr = ~0ull;
             int nk = 0;
             for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {

@@ -124,3 +124,80 @@ int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int
 }
 
 }  // namespace frnn
+
+// ---------------------------------------------------------------------------
+// Edge features for the filter stage (Sec. 3: the filter network reads the
+// graph's edges in fixed-size batches): for every edge e in [e_begin, e_end)
+// of the last build, out[(e - e_begin) * (2d + 1) + ...] = x_i[0..d), x_j[0..d),
+// d2(i, j), with d2 summed in dimension order, one rounding per operation (the
+// same value the build tested).  One warp per row: its records are contiguous.
+namespace frnn {
+namespace {
+
+__device__ __forceinline__ long long row_of_edge(const int* row_ptr, long long n, long long e)
+{
+    // largest p with row_ptr[p] <= e
+    long long lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if ((long long)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kLabelThreads) k_edge_features(DevState st, const float* emb, long long e_begin,
+                                                                 long long e_end, float* out)
+{
+    const int lane = threadIdx.x & 31;
+    const long long P = st.hdr->n_total;
+    const int B = st.hdr->n_events;
+    const int D = st.hdr->d;
+    const int W = 2 * D + 1;
+    if (P == 0 || e_end <= e_begin) return;
+    const long long p_lo = row_of_edge(st.row_ptr, P, e_begin);
+    const long long p_hi = row_of_edge(st.row_ptr, P, e_end - 1);
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long lo = 1, hi = 0, off = 0;
+    for (long long p = p_lo + (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p <= p_hi; p += nwarps) {
+        if (p < lo || p >= hi) {
+            const int b = event_of(st.ev, B, p);
+            off = st.ev[b].pt_off;
+            lo = off;
+            hi = off + st.ev[b].n;
+        }
+        const long long a = max((long long)st.row_ptr[p], e_begin);
+        const long long z = min((long long)st.row_ptr[p + 1], e_end);
+        const float* xi = emb + p * D;
+        const long long nel = (z - a) * W;
+        for (long long t = lane; t < nel; t += 32) {
+            const long long e = a + t / W;
+            const int f = (int)(t % W);
+            const float* xj = emb + (off + st.col[e]) * D;
+            float v;
+            if (f < D) {
+                v = xi[f];
+            } else if (f < 2 * D) {
+                v = xj[f - D];
+            } else {
+                float s = 0.f;
+                for (int u = 0; u < D; ++u) {
+                    const float dd = __fsub_rn(xi[u], xj[u]);
+                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+                }
+                v = s;
+            }
+            out[(e - e_begin) * W + f] = v;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_edge_features(const DevState& st, const float* emb, long long e_begin, long long e_end, float* out,
+                         int grid, void* stream)
+{
+    k_edge_features<<<grid, kLabelThreads, 0, static_cast<cudaStream_t>(stream)>>>(st, emb, e_begin, e_end, out);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace frnn

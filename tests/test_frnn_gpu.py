@@ -204,7 +204,7 @@ def test_invalid_arguments():
     plan = frnn.Plan(n_max=100, d_max=4, k_max_cap=8)
     x = torch.zeros((50, 4), device="cuda")
     try:
-        for r, k, err in [(0.0, 4, 1), (float("nan"), 4, 1), (-1.0, 4, 1), (0.1, 0, 1), (0.1, 9, 7)]:
+        for r, k, err in [(0.0, 4, 1), (float("nan"), 4, 1), (-1.0, 4, 1), (0.1, -1, 1), (0.1, 9, 7)]:
             with pytest.raises(frnn.FrnnError) as ei:
                 plan.build(x, r, k)
             assert ei.value.status == err
@@ -342,3 +342,31 @@ def test_plans_with_different_caps_coexist():
     finally:
         big.close()
         small.close()
+
+
+@pytest.mark.parametrize("kind", ["cluster", "dense"])
+def test_no_cap_rows_equal_uncapped_oracle(kind):
+    """k = FRNN_NO_CAP: the paper's own FRNN list, every neighbour within r.
+    Rows of at most 24 neighbours are sorted; longer ones are compared as sets."""
+    x = (synth.clustered_grid(5000, 8, 91, 300, 0.03, 0.1) if kind == "cluster"
+         else synth.uniform_grid(4000, 3, 92, -20, 20))
+    r = 0.1 if kind == "cluster" else 0.05
+    rp, col, d2 = oracle.radius_graph(x, r, 0, with_d2=True)
+    with frnn.Plan(n_max=x.shape[0], d_max=x.shape[1], k_max_cap=1, edge_capacity=int(rp[-1]),
+                   emit_d2=True) as plan:
+        host = plan.build(torch.from_numpy(x).cuda(), r, frnn._native.FRNN_NO_CAP).to_host()
+        assert plan.last_status() == 0
+    np.testing.assert_array_equal(host["row_ptr"], rp)
+    long_rows = 0
+    for i in range(x.shape[0]):
+        a, b = rp[i], rp[i + 1]
+        if b - a <= 24:
+            np.testing.assert_array_equal(host["col"][a:b], col[a:b])
+            np.testing.assert_array_equal(host["d2"][a:b], d2[a:b])
+        else:
+            long_rows += 1
+            o = np.argsort(host["col"][a:b])
+            assert sorted(zip(col[a:b].tolist(), d2[a:b].tolist())) == \
+                list(zip(host["col"][a:b][o].tolist(), host["d2"][a:b][o].tolist()))
+    if kind == "dense":
+        assert long_rows > 1000

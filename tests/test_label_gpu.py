@@ -51,3 +51,29 @@ def test_cut_below_radius_needs_d2():
         assert ei.value.status == frnn.FRNN_ERR_INVALID_ARG
         plan.label_components(1.0)                # every edge kept: fine
         assert plan.last_status() == 0
+
+
+def test_edge_features_in_chunks_equal_oracle():
+    """[x_i, x_j, d2] per edge, produced in fixed-size chunks as the filter
+    stage consumes them, equal the oracle's graph gathered on the host."""
+    sizes = [4000, 2500]
+    evs = [synth.clustered_grid(n, 8, 70 + i, n // 12, 0.03, 0.15) for i, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x_all = np.concatenate(evs)
+    r, k = 0.1, 16
+    xt = torch.from_numpy(x_all).cuda()
+    with frnn.Plan(n_max=int(off[-1]), d_max=8, k_max_cap=k, events_max=2) as plan:
+        csr = plan.build_batched(xt, off, r, k)
+        e_tot = csr.n_edges()
+        chunk = 7001
+        feats = torch.cat([plan.edge_features(xt, a, min(a + chunk, e_tot)) for a in range(0, e_tot, chunk)])
+        assert plan.last_status() == 0
+    feats = feats.cpu().numpy()
+    want = []
+    for b, x in enumerate(evs):
+        rp, col, d2 = oracle.radius_graph(x, r, k, with_d2=True)
+        src = np.repeat(np.arange(x.shape[0]), np.diff(rp))
+        want.append(np.concatenate([x[src], x[col], d2[:, None]], axis=1))
+    want = np.concatenate(want)
+    assert feats.shape == want.shape == (e_tot, 17)
+    np.testing.assert_array_equal(feats.view(np.uint32), want.astype(np.float32).view(np.uint32))
