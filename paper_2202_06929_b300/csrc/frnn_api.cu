@@ -301,7 +301,7 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     const unsigned long long dp = (unsigned long long)((q.d_max + 3) & ~3);
     const unsigned long long ec = (unsigned long long)q.edge_capacity;
     const unsigned long long tiles_c = (unsigned long long)(cells_max + kScanTile - 1) / kScanTile + 1;
-    const unsigned long long tiles_r = (n + kScanTile - 1) / kScanTile + 1;
+    const unsigned long long tiles_r = (n + kRowScanTile - 1) / kRowScanTile + 1;
     const bool d2 = (q.flags & FRNN_EMIT_D2) != 0;
     unsigned long long b = sizeof(CallHdr) + sizeof(EvDesc) * ev + sizeof(EvPlan) * ev;
     b += 2 * sizeof(unsigned) * ev * kMaxDims + 2 * sizeof(unsigned) * ev + sizeof(unsigned) * kCtrCount + 4;
@@ -367,7 +367,7 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     p->cells_max = cells_max;
     p->edge_cap = q.edge_capacity;
     p->tiles_cells = (int)((cells_max + kScanTile - 1) / kScanTile) + 1;
-    p->tiles_rows = (int)((q.n_max + kScanTile - 1) / kScanTile) + 1;
+    p->tiles_rows = (int)((q.n_max + kRowScanTile - 1) / kRowScanTile) + 1;
     cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, q.device);
     int rc = FRNN_OK;
     DevState& st = p->st;

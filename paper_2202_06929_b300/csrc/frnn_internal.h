@@ -10,8 +10,10 @@ constexpr int kMaxDims = 64;        // largest embedding dimension
 constexpr int kChunk = 2048;        // points per chunk of the per-point kernels
 constexpr int kPtThreads = 256;     // threads of the per-point kernels
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 8;                                  // cell scan: 2048 cells per tile
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kRowScanItems = 2;                               // row scan: 512 points per tile (it also
+constexpr int kRowScanTile = kScanThreads * kRowScanItems;     // copies their rows: more tiles, more warps)
 constexpr int kWalkThreads = 256;   // count walk: 8 warps, 32 queries per warp at a time
 constexpr int kFillThreads = 128;   // fill walk: 4 warps (more shared memory per warp)
 constexpr int kMaxDimCells = 32768; // cells along one hashed dimension (float32 key bound)
@@ -63,7 +65,7 @@ struct EvPlan {
 
 // Counter slots (all return to zero at the end of every build).
 enum { kCtrPlanned = 0, kCtrScanCellsTile, kCtrScanCellsExit, kCtrScanRowsTile,
-       kCtrScanRowsExit, kCtrCount = 8 };
+       kCtrScanRowsExit, kCtrLongRows, kCtrCount = 8 };
 
 // Device pointers owned by the plan.  Fixed for the plan's life, so a
 // captured CUDA graph of the build stays valid for every call: everything
@@ -79,11 +81,12 @@ struct DevState {
     unsigned* counters;      // [kCtrCount]
     int* cells_total;
     unsigned* key;           // [n_max] cell id of each input point (event-local)
-    unsigned* rank;          // [n_max] slot of the point inside its cell
+    unsigned* rank;          // [n_max] slot of the point inside its cell (until the scatter);
+                             // then the list of long rows (collect walk -> emit walk)
     int* perm;               // [n_max] sorted position -> event-local point index
     unsigned* cell_s;        // [n_max] sorted position -> cell id
     float* xs;               // [n_max * dp_max] points in cell order, rows padded with 0
-    int* pool_off;           // [n_max] sorted position -> first pool slot of its row, or -1
+    int* pool_off;           // [n_max] point -> first pool slot of its row, or -1
     int* cnt_o;              // [n_max] point -> min(|S_i|, k)
     int* row_ptr;            // [n_max + 1]
     unsigned* cell_count;    // [cells_max], zero between builds

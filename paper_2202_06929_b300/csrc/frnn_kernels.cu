@@ -19,9 +19,10 @@
 //                   the 3^(g-1) runs of neighbouring cells and counts the points
 //                   within r (|S_i|); rows of at most 32 neighbours are sorted
 //                   by (d2, j), cut at k and parked in a pool
-//   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr
-//   7 k_walk_emit   pooled rows copied into CSR order; longer rows walked again,
-//                   keeping the k smallest (d2, j) keys
+//   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr; each parked
+//                   row is copied to its place as soon as its offset is known
+//   7 k_walk_emit   the long rows, walked again one per warp, keeping the k
+//                   smallest (d2, j) keys
 //
 // Paper: Sec. 3.4 (fixed-radius neighbours by a grid of cells, cost growing
 // as 3^g with the gridded dimensions g, which is why at most four are used)
@@ -396,6 +397,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
     __shared__ int s_tile;
     __shared__ unsigned s_prefix;
     __shared__ int s_last;
+    // row copy of the row scan: per point of the tile its row start, pool slot
+    // and the warp-level prefix of the entries to copy
+    constexpr int IT = MODE == 0 ? kScanItems : kRowScanItems;  // items per thread
+    constexpr int TILE = kScanThreads * IT;
+    __shared__ int s_rs[MODE == 1 ? TILE : 1];
+    __shared__ int s_po[MODE == 1 ? TILE : 1];
+    __shared__ int s_pre[MODE == 1 ? TILE : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long M;
     unsigned* in;
@@ -418,33 +426,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         tile_ctr = &st.counters[kCtrScanRowsTile];
         exit_ctr = &st.counters[kCtrScanRowsExit];
     }
-    const int ntiles = (int)((M + kScanTile - 1) / kScanTile);
+    const int ntiles = (int)((M + TILE - 1) / TILE);
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
         __syncthreads();
         const int tile = s_tile;
         if (tile >= ntiles) break;
-        const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
-        unsigned v[kScanItems];
-        if (base + kScanItems <= M) {
+        const long long base = (long long)tile * TILE + (long long)threadIdx.x * IT;
+        unsigned v[IT];
+        if (IT == 8 && base + IT <= M) {
             const uint4 a = *reinterpret_cast<const uint4*>(in + base);
             const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
             v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            v[4 % IT] = b.x; v[5 % IT] = b.y; v[6 % IT] = b.z; v[7 % IT] = b.w;
             if (MODE == 0) {
                 *reinterpret_cast<uint4*>(in + base) = make_uint4(0, 0, 0, 0);
                 *reinterpret_cast<uint4*>(in + base + 4) = make_uint4(0, 0, 0, 0);
             }
+        } else if (IT == 2 && base + IT <= M) {
+            const uint2 a = *reinterpret_cast<const uint2*>(in + base);
+            v[0] = a.x;
+            v[1 % IT] = a.y;
+            if (MODE == 0) *reinterpret_cast<uint2*>(in + base) = make_uint2(0, 0);
         } else {
 #pragma unroll
-            for (int i = 0; i < kScanItems; ++i) {
+            for (int i = 0; i < IT; ++i) {
                 v[i] = (base + i < M) ? in[base + i] : 0u;
                 if (MODE == 0 && base + i < M) in[base + i] = 0u;
             }
         }
         unsigned tsum = 0;
 #pragma unroll
-        for (int i = 0; i < kScanItems; ++i) tsum += v[i];
+        for (int i = 0; i < IT; ++i) tsum += v[i];
         unsigned total;
         const unsigned texcl = block_excl_scan(tsum, &total);
         if (warp == 0) {
@@ -461,9 +474,56 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         __syncthreads();
         unsigned run = s_prefix + texcl;
 #pragma unroll
-        for (int i = 0; i < kScanItems; ++i) {
+        for (int i = 0; i < IT; ++i) {
             if (base + i < M) out[base + i] = (int)run;
             run += v[i];
+        }
+        if (MODE == 1) {
+            // Rows parked by the collect walk go to their place as soon as
+            // their offsets are known (long rows are left to the emit walk).
+            // Each warp streams the entries of its 256 points: element e of
+            // the warp's list belongs to the point found by binary search over
+            // the warp's prefix sums, so loads and stores are coalesced.
+            const long long ecap = st.hdr->edge_capacity;
+            const int emit = st.hdr->emit_d2;
+            unsigned rs = s_prefix + texcl;
+            int mine = 0;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                const long long p = base + i;
+                const int loc = threadIdx.x * IT + i;
+                int c = 0, po = -1;
+                if (p < M && v[i] > 0u && (long long)rs + v[i] <= ecap) {
+                    po = st.pool_off[p];
+                    if (po >= 0) c = (int)v[i];
+                }
+                s_rs[loc] = (int)rs;
+                s_po[loc] = po;
+                s_pre[loc] = mine;  // exclusive within the thread for now
+                mine += c;
+                rs += v[i];
+            }
+            const int wexcl = warp_incl_scan(mine, lane) - mine;
+            const int wtot = __shfl_sync(kFull, wexcl + mine, 31);
+#pragma unroll
+            for (int i = 0; i < IT; ++i) s_pre[threadIdx.x * IT + i] += wexcl;
+            __syncwarp();
+            const int* pre = s_pre + warp * 32 * IT;
+            const int* wrs = s_rs + warp * 32 * IT;
+            const int* wpo = s_po + warp * 32 * IT;
+#pragma unroll 4
+            for (int e = lane; e < wtot; e += 32) {
+                int lo = 0, hi = 32 * IT - 1;  // last point with pre <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pre[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                const int t = e - pre[lo];
+                const int src = wpo[lo] + t;
+                const int dst = wrs[lo] + t;
+                st.col[dst] = st.pool[src];
+                if (emit) st.d2[dst] = st.pool_d2[src];
+            }
         }
         __syncthreads();
     }
@@ -482,6 +542,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         out[M] = (int)last_incl;
         *tile_ctr = 0u;
         *exit_ctr = 0u;
+        if (MODE == 0) st.counters[kCtrLongRows] = 0u;  // the emit walk of the last build is done with it
     }
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
     if (MODE == 1) {
@@ -973,8 +1034,17 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
         const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
         const int self_j = valid ? __ldg(st.perm + q) : -1;
         if (valid) {
-            st.pool_off[q] = my_off;
+            st.pool_off[le.pt_off + self_j] = my_off;
             st.cnt_o[le.pt_off + self_j] = cnt;
+        }
+        // rows that were not parked go on the emit walk's list
+        const bool longrow = valid && cnt > 0 && my_off < 0;
+        const unsigned lm = __ballot_sync(kFull, longrow);
+        if (lm) {
+            unsigned lbase = 0;
+            if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
+            lbase = __shfl_sync(kFull, lbase, 0);
+            if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
         }
         __syncwarp();
         // every lane sorts its own row (insertion sort, at most kRowSlots keys);
@@ -1014,9 +1084,9 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     }
 }
 
-// Stage 7: rows in CSR order.  Pooled rows are copied; the others (|S_i| >
-// kFast, or no pool space) walk their cell's runs again, one query at a time,
-// keeping the k smallest keys.
+// Stage 7: the long rows (more than kFast neighbours, or no pool space), one
+// warp per row from the collect walk's list: walk the row's cell runs again
+// and keep the k smallest keys (or, with no cap, every neighbour).
 template <int DP4>
 __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(DevState st, int cap)
 {
@@ -1024,147 +1094,113 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (32 * DP);
+    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (2 * DP);
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(
-        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (32 * DP)) + (size_t)wib * cap;
+        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (2 * DP)) + (size_t)wib * cap;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
     const int K = st.hdr->k;
     const int B = st.hdr->n_events;
     const int emit = st.hdr->emit_d2;
     const long long ecap = st.hdr->edge_capacity;
-    const long long nchunks = (P + 31) >> 5;
-    const long long nwarps = (long long)gridDim.x * (kFillThreads / 32);
+    const int n_long = (int)st.counters[kCtrLongRows];
+    const int nwarps = gridDim.x * (kFillThreads / 32);
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
-    LaneEvent le;
-    le.lo = 1;
-    le.hi = 0;
     __shared__ WarpWalk s_ww[kFillThreads / 32];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    for (long long ch = (long long)blockIdx.x * (kFillThreads / 32) + wib; ch < nchunks; ch += nwarps) {
-        const long long q0 = ch << 5;
-        const long long q = q0 + lane;
-        const bool valid = q < P;
-        lane_event(st.ev, B, valid ? q : P - 1, le);
-        int rs = 0, cnt = 0, po = -1;
-        if (valid) {
-            const long long p = le.pt_off + __ldg(st.perm + q);
-            rs = st.row_ptr[p];
-            const int re = st.row_ptr[p + 1];
-            cnt = ((long long)re <= ecap) ? re - rs : 0;  // over capacity: OVERFLOW already latched
-            po = st.pool_off[q];
+    for (int li = blockIdx.x * (kFillThreads / 32) + wib; li < n_long; li += nwarps) {
+        const long long q = (long long)st.rank[li];
+        const int b = event_of_point(st.ev, B, q);
+        const long long p = st.ev[b].pt_off + __ldg(st.perm + q);
+        const int rsi = st.row_ptr[p];
+        const int re = st.row_ptr[p + 1];
+        if ((long long)re > ecap) continue;  // over capacity: OVERFLOW already latched
+        const int cnti = re - rsi;
+        // the query's coordinates, in slot 0 of a pair row
+        __syncwarp();
+        if (lane < DP4) {
+            const float4 v = __ldg(xs4 + q * DP4 + lane);
+            sq[2 * (4 * lane + 0)] = v.x;
+            sq[2 * (4 * lane + 1)] = v.y;
+            sq[2 * (4 * lane + 2)] = v.z;
+            sq[2 * (4 * lane + 3)] = v.w;
         }
-        // pooled rows: the chunk's rows lie back to back in the pool, in lane
-        // order, so the warp streams them with coalesced loads
-        {
-            const bool pooled = cnt > 0 && po >= 0;
-            const int need = pooled ? cnt : 0;
-            const int incl = warp_incl_scan(need, lane);
-            const int tot = __shfl_sync(kFull, incl, 31);
-            if (tot > 0) {
-                // element e of the chunk's list belongs to lane r = find_run(incl, e)
-                const int rel = rs - (incl - need);  // its destination: rel_r + e
-                const int srel = po - (incl - need);  // its pool slot: srel_r + e
-#pragma unroll 2
-                for (int base = 0; base < tot; base += 32) {
-                    const int e2 = base + lane;
-                    const int r = find_run(incl, e2);
-                    const int dst = __shfl_sync(kFull, rel, r) + e2;
-                    const int src = __shfl_sync(kFull, srel, r) + e2;
-                    if (e2 < tot) {
-                        st.col[dst] = st.pool[src];
-                        if (emit) st.d2[dst] = st.pool_d2[src];
-                    }
-                }
-            }
+        __syncwarp();
+        if (b != plan_b) {
+            load_plan(ww, st.plan, b, lane);
+            plan_b = b;
         }
-        unsigned wm = __ballot_sync(kFull, cnt > 0 && po < 0);
-        if (!wm) continue;
-        stage_queries<DP4>(xs4, q, valid, sq, lane);
-        while (wm) {
-            const int i = __ffs(wm) - 1;
-            wm &= wm - 1;
-            const int sb = __shfl_sync(kFull, le.b, i);
-            const int rsi = __shfl_sync(kFull, rs, i);
-            const int cnti = __shfl_sync(kFull, cnt, i);
-            if (sb != plan_b) {
-                load_plan(ww, st.plan, sb, lane);
-                plan_b = sb;
-            }
-            const float* qrow = sq + (i >> 1) * (2 * DP);
-            const int half = i & 1;
-            segment_cell(ww, qrow, half, lane);
-            if (K == 0x7fffffff) {
-                // no cap: the whole row, written in candidate order
-                int nw = 0;
-                for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
-                for (int base = 0; base < rn.total; base += 32) {
-                    const int cand = candidate_at(rn, base + lane);
-                    float d2 = 0.f;
-                    bool take = false;
-                    if (cand >= 0) {
-                        d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
-                        take = d2 <= r2 && (long long)cand != q0 + i;
-                    }
-                    const unsigned m = __ballot_sync(kFull, take);
-                    const int slot = nw + __popc(m & lt_mask);
-                    if (take && slot < cnti) {
-                        st.col[rsi + slot] = __ldg(st.perm + cand);
-                        if (emit) st.d2[rsi + slot] = d2;
-                    }
-                    nw += __popc(m);
-                }
-                });
-                continue;
-            }
-            unsigned long long thr = ~0ull;
-            int nk = 0;
+        const float* qrow = sq;
+        const int half = 0;
+        segment_cell(ww, qrow, half, lane);
+        if (K == 0x7fffffff) {
+            // no cap: the whole row, written in candidate order
+            int nw = 0;
             for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
-                unsigned long long key = ~0ull;
+                float d2 = 0.f;
                 bool take = false;
                 if (cand >= 0) {
-                    const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
-                    if (d2 <= r2 && (long long)cand != q0 + i) {
-                        key = edge_key(d2, __ldg(st.perm + cand));
-                        take = key < thr;
-                    }
+                    d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
+                    take = d2 <= r2 && (long long)cand != q;
                 }
-                unsigned m = __ballot_sync(kFull, take);
-                if (m == 0u) continue;
-                if (nk + 32 > cap) {
-                    // only reached when |S_i| > k: keep the k smallest so far
-                    warp_sort_smem(keys, nk, lane);
-                    nk = K;
-                    thr = keys[K - 1];
-                    take = take && (key < thr);
-                    m = __ballot_sync(kFull, take);
+                const unsigned m = __ballot_sync(kFull, take);
+                const int slot = nw + __popc(m & lt_mask);
+                if (take && slot < cnti) {
+                    st.col[rsi + slot] = __ldg(st.perm + cand);
+                    if (emit) st.d2[rsi + slot] = d2;
                 }
-                if (take) keys[nk + __popc(m & lt_mask)] = key;
-                nk += __popc(m);
-                __syncwarp();
+                nw += __popc(m);
             }
             });
-            const int nout = min(cnti, nk);
-            if (nk <= 32) {
-                unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
-                v = warp_sort32(v, lane);
-                if (lane < nout) {
-                    st.col[rsi + lane] = (int)(unsigned)v;
-                    if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
-                }
-            } else {
-                warp_sort_smem(keys, nk, lane);
-                for (int e2 = lane; e2 < nout; e2 += 32) {
-                    const unsigned long long v = keys[e2];
-                    st.col[rsi + e2] = (int)(unsigned)v;
-                    if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
+            continue;
+        }
+        unsigned long long thr = ~0ull;
+        int nk = 0;
+        for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
+        for (int base = 0; base < rn.total; base += 32) {
+            const int cand = candidate_at(rn, base + lane);
+            unsigned long long key = ~0ull;
+            bool take = false;
+            if (cand >= 0) {
+                const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
+                if (d2 <= r2 && (long long)cand != q) {
+                    key = edge_key(d2, __ldg(st.perm + cand));
+                    take = key < thr;
                 }
             }
+            unsigned m = __ballot_sync(kFull, take);
+            if (m == 0u) continue;
+            if (nk + 32 > cap) {
+                // only reached when |S_i| > k: keep the k smallest so far
+                warp_sort_smem(keys, nk, lane);
+                nk = K;
+                thr = keys[K - 1];
+                take = take && (key < thr);
+                m = __ballot_sync(kFull, take);
+            }
+            if (take) keys[nk + __popc(m & lt_mask)] = key;
+            nk += __popc(m);
             __syncwarp();
+        }
+        });
+        const int nout = min(cnti, nk);
+        if (nk <= 32) {
+            unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
+            v = warp_sort32(v, lane);
+            if (lane < nout) {
+                st.col[rsi + lane] = (int)(unsigned)v;
+                if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
+            }
+        } else {
+            warp_sort_smem(keys, nk, lane);
+            for (int e2 = lane; e2 < nout; e2 += 32) {
+                const unsigned long long v = keys[e2];
+                st.col[rsi + e2] = (int)(unsigned)v;
+                if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
+            }
         }
         __syncwarp();
     }
@@ -1186,7 +1222,7 @@ int collect_smem()
 template <int DP4>
 int emit_smem(int cap)
 {
-    return (kFillThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + cap * (int)sizeof(unsigned long long));
+    return (kFillThreads / 32) * (2 * 4 * DP4 * (int)sizeof(float) + cap * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>

@@ -62,7 +62,7 @@ constexpr size_t kOffXs = align256(kOffCntO + sizeof(int) * kNoallocMaxPoints);
 constexpr size_t kOffCellCount = align256(kOffXs + sizeof(float) * kNoallocMaxPoints * kNoallocMaxDims);
 constexpr size_t kOffCellStart = align256(kOffCellCount + sizeof(unsigned) * kNoallocCells);
 constexpr long long kTilesCells = kNoallocCells / kScanTile + 1;
-constexpr long long kTilesRows = kNoallocMaxPoints / kScanTile + 1;
+constexpr long long kTilesRows = kNoallocMaxPoints / kRowScanTile + 1;
 constexpr size_t kOffScanCells = align256(kOffCellStart + sizeof(int) * (kNoallocCells + 1));
 constexpr size_t kOffScanRows = align256(kOffScanCells + sizeof(unsigned long long) * kTilesCells);
 constexpr size_t kOffPool = align256(kOffScanRows + sizeof(unsigned long long) * kTilesRows);
