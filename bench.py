@@ -49,7 +49,7 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM read + write bytes per point of the collect walk, from the ncu capture
 # summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
 # kernel source it was taken on (traffic scales with the points processed).
-MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "42e62d75880b", "bytes_per_point": 429_538_816 / 4_800_000}
+MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "04fe1fa2c75d", "bytes_per_point": 446_506_752 / 4_800_000}
 
 
 def parse_args(argv=None):
