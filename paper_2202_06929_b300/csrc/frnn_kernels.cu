@@ -250,27 +250,53 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
         const float* base = h.emb + (e.pt_off + first) * D;
         const int nel = np * D;
         bool nf = false;
-        if ((kPtThreads % D) == 0) {
-            // every element this thread reads belongs to dim threadIdx.x % D
-            unsigned lmin = 0xffffffffu, lmax = 0u;
-            for (int i = threadIdx.x; i < nel; i += kPtThreads) {
-                const float v = __ldg(base + i);
-                nf |= !isfinite(v);
-                const unsigned u = f2ord(v);
-                lmin = min(lmin, u);
-                lmax = max(lmax, u);
-            }
-            if (threadIdx.x < nel) {
-                atomicMin(&s_min[threadIdx.x % D], lmin);
-                atomicMax(&s_max[threadIdx.x % D], lmax);
+        const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
+        if (vec) {
+            // float4 loads; with S a multiple of D / 4, every float4 this
+            // thread reads holds dims 4 (threadIdx.x % (D / 4)) .. + 3
+            const int q4 = D >> 2;
+            const int S = (kPtThreads / q4) * q4;
+            const float4* b4 = reinterpret_cast<const float4*>(base);
+            const int n4 = np * q4;
+            unsigned mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mn3 = 0xffffffffu;
+            unsigned mx0 = 0u, mx1 = 0u, mx2 = 0u, mx3 = 0u;
+            if ((int)threadIdx.x < S) {
+#pragma unroll 4
+                for (int i = threadIdx.x; i < n4; i += S) {
+                    const float4 v = __ldg(b4 + i);
+                    nf |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+                    const unsigned u0 = f2ord(v.x), u1 = f2ord(v.y), u2 = f2ord(v.z), u3 = f2ord(v.w);
+                    mn0 = min(mn0, u0); mx0 = max(mx0, u0);
+                    mn1 = min(mn1, u1); mx1 = max(mx1, u1);
+                    mn2 = min(mn2, u2); mx2 = max(mx2, u2);
+                    mn3 = min(mn3, u3); mx3 = max(mx3, u3);
+                }
+                if ((int)threadIdx.x < n4) {
+                    const int d0 = 4 * ((int)threadIdx.x % q4);
+                    atomicMin(&s_min[d0 + 0], mn0); atomicMax(&s_max[d0 + 0], mx0);
+                    atomicMin(&s_min[d0 + 1], mn1); atomicMax(&s_max[d0 + 1], mx1);
+                    atomicMin(&s_min[d0 + 2], mn2); atomicMax(&s_max[d0 + 2], mx2);
+                    atomicMin(&s_min[d0 + 3], mn3); atomicMax(&s_max[d0 + 3], mx3);
+                }
             }
         } else {
-            for (int i = threadIdx.x; i < nel; i += kPtThreads) {
-                const float v = __ldg(base + i);
-                nf |= !isfinite(v);
-                const unsigned u = f2ord(v);
-                atomicMin(&s_min[i % D], u);
-                atomicMax(&s_max[i % D], u);
+            // with S a multiple of D, every element this thread reads belongs
+            // to dim threadIdx.x % D
+            const int S = (kPtThreads / D) * D;
+            unsigned lmin = 0xffffffffu, lmax = 0u;
+            if ((int)threadIdx.x < S) {
+#pragma unroll 4
+                for (int i = threadIdx.x; i < nel; i += S) {
+                    const float v = __ldg(base + i);
+                    nf |= !isfinite(v);
+                    const unsigned u = f2ord(v);
+                    lmin = min(lmin, u);
+                    lmax = max(lmax, u);
+                }
+                if ((int)threadIdx.x < nel) {
+                    atomicMin(&s_min[threadIdx.x % D], lmin);
+                    atomicMax(&s_max[threadIdx.x % D], lmax);
+                }
             }
         }
         if (nf) s_nf = 1;
@@ -322,31 +348,59 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float inv_s, int nc
     return (a < (float)ncell) ? (int)a : ncell - 1;  // a >= 0: truncation is floor
 }
 
-__global__ void __launch_bounds__(kPtThreads) k_key_hist(DevState st)
+// Points handled per thread at a time by the per-point kernels: their loads
+// are all issued before any result is used.
+constexpr int kPtBatch = 4;
+
+__global__ void __launch_bounds__(kPtThreads, 4) k_key_hist(DevState st)
 {
+    __shared__ EvPlan s_pl;  // the chunk's event plan (all threads of a block share one chunk)
     const CallHdr h = *st.hdr;
     const int D = h.d;
     for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
-        const EvPlan pl = st.plan[b];
+        __syncthreads();  // the previous chunk is done with s_pl
+        if (threadIdx.x == 0) s_pl = st.plan[b];
+        __syncthreads();
+        const EvPlan& pl = s_pl;
         const long long first = (long long)(c - e.chunk_off) * kChunk;
         const long long rem = (long long)e.n - first;
         const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
-        for (int i = threadIdx.x; i < np; i += kPtThreads) {
-            const long long p = e.pt_off + first + i;
-            const float* x = h.emb + p * D;
-            unsigned cid = 0;
-            if (!pl.skip) {
+        for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
+            float xv[kPtBatch][kMaxG];
 #pragma unroll
-                for (int t = 0; t < kMaxG; ++t) {
-                    if (t < pl.g)
-                        cid += (unsigned)(cell_coord(__ldg(x + pl.dims[t]), pl.lo[t], pl.inv_s,
-                                                     pl.ncell[t]) * pl.stride[t]);
+            for (int u = 0; u < kPtBatch; ++u) {
+                const int i = i0 + u * kPtThreads;
+                const float* x = h.emb + (e.pt_off + first + (i < np ? i : 0)) * D;
+#pragma unroll
+                for (int t = 0; t < kMaxG; ++t) xv[u][t] = (i < np && t < pl.g) ? __ldg(x + pl.dims[t]) : 0.f;
+            }
+            unsigned cid[kPtBatch];
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u) {
+                cid[u] = 0;
+                if (!pl.skip) {
+#pragma unroll
+                    for (int t = 0; t < kMaxG; ++t) {
+                        if (t < pl.g)
+                            cid[u] += (unsigned)(cell_coord(xv[u][t], pl.lo[t], pl.inv_s, pl.ncell[t]) * pl.stride[t]);
+                    }
                 }
             }
-            st.key[p] = cid;
-            st.rank[p] = atomicAdd(&st.cell_count[pl.cell_off + cid], 1u);
+            unsigned rk[kPtBatch];
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u)
+                rk[u] = (i0 + u * kPtThreads < np) ? atomicAdd(&st.cell_count[pl.cell_off + cid[u]], 1u) : 0u;
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u) {
+                const int i = i0 + u * kPtThreads;
+                if (i < np) {
+                    const long long p = e.pt_off + first + i;
+                    st.key[p] = cid[u];
+                    st.rank[p] = rk[u];
+                }
+            }
         }
     }
 }
@@ -362,48 +416,94 @@ __global__ void __launch_bounds__(kPtThreads) k_key_hist(DevState st)
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 
-__device__ unsigned lookback(unsigned long long* state, int tile, int lane, unsigned* status)
+// Block-wide look-back: thread t reads the state of tile (top - t), so one
+// round covers blockDim.x predecessors.  The nearest tile that holds an
+// inclusive prefix ends the walk; the tiles above it add their aggregates.
+// (With hundreds of tiles in flight a 32-wide window needs many rounds of L2
+// latency per tile, and those rounds bounded the scans' throughput.)  Every
+// thread returns the same prefix.
+__device__ unsigned block_lookback(unsigned long long* state, int tile, unsigned* status)
 {
+    __shared__ int s_first[32];
+    __shared__ unsigned s_part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (int)(blockDim.x >> 5);
+    constexpr int kNone = 0x7fffffff;
     unsigned prefix = 0;
     int top = tile - 1;
     for (;;) {
-        const int idx = top - lane;
+        const int idx = top - (int)threadIdx.x;
         unsigned long long s = 0;
         int spins = 0;
         for (;;) {
-            s = (idx >= 0) ? ld_relaxed(state + idx) : kFlagPre;
-            if (__all_sync(kFull, (s >> 62) != 0)) break;
-            if (++spins > kSpinLimit) {
-                if (lane == 0) atomicOr(status, kStTimeout);
+            s = (idx >= 0) ? ld_relaxed(state + idx) : kFlagPre;  // before tile 0: prefix 0
+            if (__syncthreads_and((s >> 62) != 0)) break;
+            if (++spins > kSpinLimit) {  // uniform across the block
+                if (threadIdx.x == 0) atomicOr(status, kStTimeout);
                 return prefix;
             }
             __nanosleep(32);
         }
-        const unsigned pmask = __ballot_sync(kFull, (s >> 62) == 2);
-        const unsigned v = (unsigned)s;
-        if (pmask) {
-            const int first = __ffs(pmask) - 1;
-            prefix += warp_sum(lane <= first ? v : 0u);
-            return prefix;
-        }
-        prefix += warp_sum(v);
-        top -= 32;
+        const unsigned pm = __ballot_sync(kFull, (s >> 62) == 2);
+        if (lane == 0) s_first[warp] = pm ? warp * 32 + __ffs(pm) - 1 : kNone;
+        __syncthreads();
+        int first = kNone;
+        for (int w = 0; w < nw; ++w) first = min(first, s_first[w]);
+        const unsigned part = warp_sum((int)threadIdx.x <= first ? (unsigned)s : 0u);
+        if (lane == 0) s_part[warp] = part;
+        __syncthreads();
+        for (int w = 0; w < nw; ++w) prefix += s_part[w];
+        if (first != kNone) return prefix;
+        top -= (int)blockDim.x;
     }
 }
 
+// Items [base, base + IT) of the scan input (0 past the end); the cell scan
+// also clears them (the histogram must be zero for the next build).
+template <int MODE, int IT>
+__device__ __forceinline__ void scan_load(unsigned* in, long long base, long long M, bool clear, unsigned (&v)[IT])
+{
+    if (IT == 8 && base + IT <= M) {
+        const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+        const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
+        v[0] = a.x; v[1 % IT] = a.y; v[2 % IT] = a.z; v[3 % IT] = a.w;
+        v[4 % IT] = b.x; v[5 % IT] = b.y; v[6 % IT] = b.z; v[7 % IT] = b.w;
+        if (MODE == 0 && clear) {
+            *reinterpret_cast<uint4*>(in + base) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(in + base + 4) = make_uint4(0, 0, 0, 0);
+        }
+    } else if (IT == 2 && base + IT <= M) {
+        const uint2 a = *reinterpret_cast<const uint2*>(in + base);
+        v[0] = a.x;
+        v[1 % IT] = a.y;
+        if (MODE == 0 && clear) *reinterpret_cast<uint2*>(in + base) = make_uint2(0, 0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            v[i] = (base + i < M) ? in[base + i] : 0u;
+            if (MODE == 0 && clear && base + i < M) in[base + i] = 0u;
+        }
+    }
+}
+
+// Exclusive scan with one look-back per block-sized share of the input: a
+// block takes a tile (a run of sub-tiles of kScanThreads x IT items) from a
+// counter, sums it (first pass), publishes the sum and looks back once, then
+// scans its sub-tiles in order (second pass, mostly from L2).  Tiles are
+// sized so that about one goes to each block; a tile only waits for tiles
+// taken before it, which running blocks hold.
 template <int MODE>
 __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
 {
     __shared__ int s_tile;
-    __shared__ unsigned s_prefix;
     __shared__ int s_last;
-    // row copy of the row scan: per point of the tile its row start, pool slot
-    // and the warp-level prefix of the entries to copy
+    // row copy of the row scan: per point of the sub-tile its row start, pool
+    // slot and the warp-level prefix of the entries to copy
     constexpr int IT = MODE == 0 ? kScanItems : kRowScanItems;  // items per thread
-    constexpr int TILE = kScanThreads * IT;
-    __shared__ int s_rs[MODE == 1 ? TILE : 1];
-    __shared__ int s_po[MODE == 1 ? TILE : 1];
-    __shared__ int s_pre[MODE == 1 ? TILE : 1];
+    constexpr int SUB = kScanThreads * IT;
+    __shared__ int s_rs[MODE == 1 ? SUB : 1];
+    __shared__ int s_po[MODE == 1 ? SUB : 1];
+    __shared__ int s_pre[MODE == 1 ? SUB : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long M;
     unsigned* in;
@@ -426,104 +526,118 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         tile_ctr = &st.counters[kCtrScanRowsTile];
         exit_ctr = &st.counters[kCtrScanRowsExit];
     }
-    const int ntiles = (int)((M + TILE - 1) / TILE);
+    const long long nsub = (M + SUB - 1) / SUB;
+    const long long spt = (nsub + gridDim.x - 1) / gridDim.x;  // sub-tiles per tile
+    const int ntiles = (int)(spt > 0 ? (nsub + spt - 1) / spt : 0);
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
         __syncthreads();
         const int tile = s_tile;
         if (tile >= ntiles) break;
-        const long long base = (long long)tile * TILE + (long long)threadIdx.x * IT;
-        unsigned v[IT];
-        if (IT == 8 && base + IT <= M) {
-            const uint4 a = *reinterpret_cast<const uint4*>(in + base);
-            const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4 % IT] = b.x; v[5 % IT] = b.y; v[6 % IT] = b.z; v[7 % IT] = b.w;
-            if (MODE == 0) {
-                *reinterpret_cast<uint4*>(in + base) = make_uint4(0, 0, 0, 0);
-                *reinterpret_cast<uint4*>(in + base + 4) = make_uint4(0, 0, 0, 0);
-            }
-        } else if (IT == 2 && base + IT <= M) {
-            const uint2 a = *reinterpret_cast<const uint2*>(in + base);
-            v[0] = a.x;
-            v[1 % IT] = a.y;
-            if (MODE == 0) *reinterpret_cast<uint2*>(in + base) = make_uint2(0, 0);
-        } else {
-#pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                v[i] = (base + i < M) ? in[base + i] : 0u;
-                if (MODE == 0 && base + i < M) in[base + i] = 0u;
-            }
-        }
+        const long long sub0 = (long long)tile * spt;
+        const long long sub1 = min(sub0 + spt, nsub);
+        // first pass: the tile's sum
         unsigned tsum = 0;
+#pragma unroll 4
+        for (long long sb = sub0; sb < sub1; ++sb) {
+            unsigned v[IT];
+            scan_load<MODE, IT>(in, sb * SUB + (long long)threadIdx.x * IT, M, false, v);
 #pragma unroll
-        for (int i = 0; i < IT; ++i) tsum += v[i];
+            for (int i = 0; i < IT; ++i) tsum += v[i];
+        }
         unsigned total;
-        const unsigned texcl = block_excl_scan(tsum, &total);
-        if (warp == 0) {
-            unsigned prefix = 0;
-            if (tile == 0) {
-                if (lane == 0) st_relaxed(state, kFlagPre | total);
-            } else {
-                if (lane == 0) st_relaxed(state + tile, kFlagAgg | total);
-                prefix = lookback(state, tile, lane, st.status);
-                if (lane == 0) st_relaxed(state + tile, kFlagPre | (unsigned)(prefix + total));
-            }
-            if (lane == 0) s_prefix = prefix;
+        block_excl_scan(tsum, &total);
+        unsigned prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) st_relaxed(state, kFlagPre | total);
+        } else {
+            if (threadIdx.x == 0) st_relaxed(state + tile, kFlagAgg | total);
+            prefix = block_lookback(state, tile, st.status);
+            if (threadIdx.x == 0) st_relaxed(state + tile, kFlagPre | (unsigned)(prefix + total));
         }
-        __syncthreads();
-        unsigned run = s_prefix + texcl;
+        // second pass: scan the sub-tiles in order
+        for (long long sb = sub0; sb < sub1; ++sb) {
+            const long long base = sb * SUB + (long long)threadIdx.x * IT;
+            unsigned v[IT];
+            scan_load<MODE, IT>(in, base, M, true, v);
+            int po[IT];  // row scan: pool slots (they do not depend on the scan)
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            if (base + i < M) out[base + i] = (int)run;
-            run += v[i];
-        }
-        if (MODE == 1) {
-            // Rows parked by the collect walk go to their place as soon as
-            // their offsets are known (long rows are left to the emit walk).
-            // Each warp streams the entries of its 256 points: element e of
-            // the warp's list belongs to the point found by binary search over
-            // the warp's prefix sums, so loads and stores are coalesced.
-            const long long ecap = st.hdr->edge_capacity;
-            const int emit = st.hdr->emit_d2;
-            unsigned rs = s_prefix + texcl;
-            int mine = 0;
+            for (int i = 0; i < IT; ++i) po[i] = (MODE == 1 && base + i < M) ? __ldg(st.pool_off + base + i) : -1;
+            unsigned ssum = 0;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) ssum += v[i];
+            unsigned stot;
+            const unsigned texcl = block_excl_scan(ssum, &stot);
+            unsigned run = prefix + texcl;
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
-                const long long p = base + i;
-                const int loc = threadIdx.x * IT + i;
-                int c = 0, po = -1;
-                if (p < M && v[i] > 0u && (long long)rs + v[i] <= ecap) {
-                    po = st.pool_off[p];
-                    if (po >= 0) c = (int)v[i];
-                }
-                s_rs[loc] = (int)rs;
-                s_po[loc] = po;
-                s_pre[loc] = mine;  // exclusive within the thread for now
-                mine += c;
-                rs += v[i];
+                if (base + i < M) out[base + i] = (int)run;
+                run += v[i];
             }
-            const int wexcl = warp_incl_scan(mine, lane) - mine;
-            const int wtot = __shfl_sync(kFull, wexcl + mine, 31);
+            if (MODE == 1) {
+                // Rows parked by the collect walk go to their place as soon as
+                // their offsets are known (long rows are left to the emit walk).
+                // Each warp streams the entries of its 32 x IT points: element e
+                // of the warp's list belongs to the point found by binary search
+                // over the warp's prefix sums, so loads and stores are coalesced.
+                const long long ecap = st.hdr->edge_capacity;
+                const int emit = st.hdr->emit_d2;
+                unsigned rs = prefix + texcl;
+                int mine = 0;
 #pragma unroll
-            for (int i = 0; i < IT; ++i) s_pre[threadIdx.x * IT + i] += wexcl;
-            __syncwarp();
-            const int* pre = s_pre + warp * 32 * IT;
-            const int* wrs = s_rs + warp * 32 * IT;
-            const int* wpo = s_po + warp * 32 * IT;
-#pragma unroll 4
-            for (int e = lane; e < wtot; e += 32) {
-                int lo = 0, hi = 32 * IT - 1;  // last point with pre <= e
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (pre[mid] <= e) lo = mid; else hi = mid - 1;
+                for (int i = 0; i < IT; ++i) {
+                    const int loc = threadIdx.x * IT + i;
+                    const bool cp = base + i < M && v[i] > 0u && (long long)rs + v[i] <= ecap && po[i] >= 0;
+                    s_rs[loc] = (int)rs;
+                    s_po[loc] = po[i];
+                    s_pre[loc] = mine;  // exclusive within the thread for now
+                    mine += cp ? (int)v[i] : 0;
+                    rs += v[i];
                 }
-                const int t = e - pre[lo];
-                const int src = wpo[lo] + t;
-                const int dst = wrs[lo] + t;
-                st.col[dst] = st.pool[src];
-                if (emit) st.d2[dst] = st.pool_d2[src];
+                const int wexcl = warp_incl_scan(mine, lane) - mine;
+                const int wtot = __shfl_sync(kFull, wexcl + mine, 31);
+#pragma unroll
+                for (int i = 0; i < IT; ++i) s_pre[threadIdx.x * IT + i] += wexcl;
+                __syncwarp();
+                constexpr int WP = 32 * IT;  // points of the warp
+                const int* pre = s_pre + warp * WP;
+                const int* wrs = s_rs + warp * WP;
+                const int* wpo = s_po + warp * WP;
+                // kCopyBatch entries per lane at a time: all sources are located
+                // first, then all loads issued, then all stores (the pool reads
+                // are gathers, so latency is hidden by having many in flight).
+                constexpr int kCopyBatch = 8;
+                for (int e0 = 0; e0 < wtot; e0 += 32 * kCopyBatch) {
+                    int src[kCopyBatch], dst[kCopyBatch];
+#pragma unroll
+                    for (int u = 0; u < kCopyBatch; ++u) {
+                        const int e = e0 + u * 32 + lane;
+                        int lo = 0;  // last point of the warp with pre <= e (pre[0] = 0)
+#pragma unroll
+                        for (int step = WP / 2; step >= 1; step >>= 1)
+                            if (pre[lo + step] <= e) lo += step;
+                        const int t = e - pre[lo];
+                        src[u] = e < wtot ? wpo[lo] + t : -1;
+                        dst[u] = wrs[lo] + t;
+                    }
+                    int cv[kCopyBatch];
+                    float dv[kCopyBatch];
+#pragma unroll
+                    for (int u = 0; u < kCopyBatch; ++u) {
+                        cv[u] = src[u] >= 0 ? __ldg(st.pool + src[u]) : 0;
+                        dv[u] = (emit && src[u] >= 0) ? __ldg(st.pool_d2 + src[u]) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kCopyBatch; ++u) {
+                        if (src[u] >= 0) {
+                            st.col[dst[u]] = cv[u];
+                            if (emit) st.d2[dst[u]] = dv[u];
+                        }
+                    }
+                }
+                __syncwarp();  // s_pre / s_rs / s_po are rewritten by the next sub-tile
             }
+            prefix += stot;
         }
         __syncthreads();
     }
@@ -561,11 +675,51 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
 // --------------------------------------------------------------------------
 // Stage 4: scatter into cell order.
 
+// 32-byte global accesses (one instruction per 8-float row; both addresses
+// must be 32-byte aligned).
+struct F8 {
+    float v[8];
+};
+__device__ __forceinline__ F8 ld_nc_f8(const float* p)
+{
+    F8 r;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+          "=f"(r.v[7])
+        : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void st_f8(float* p, const F8& r)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(r.v[0]), "f"(r.v[1]),
+                 "f"(r.v[2]), "f"(r.v[3]), "f"(r.v[4]), "f"(r.v[5]), "f"(r.v[6]), "f"(r.v[7])
+                 : "memory");
+}
+
+// Copy of one point's row into xs (padded to dp floats with zeros).
+__device__ __forceinline__ void copy_row(const float* x, float4* dst, int D, int dp, bool vec)
+{
+    if (vec) {
+        const float4* src = reinterpret_cast<const float4*>(x);
+        for (int t = 0; t < dp / 4; ++t) dst[t] = __ldg(src + t);
+    } else {
+        for (int t = 0; t < dp; t += 4) {
+            float4 w;
+            w.x = (t + 0 < D) ? __ldg(x + t + 0) : 0.f;
+            w.y = (t + 1 < D) ? __ldg(x + t + 1) : 0.f;
+            w.z = (t + 2 < D) ? __ldg(x + t + 2) : 0.f;
+            w.w = (t + 3 < D) ? __ldg(x + t + 3) : 0.f;
+            dst[t / 4] = w;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 {
     const CallHdr h = *st.hdr;
     const int D = h.d, dp = h.dp;
     const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
+    const bool vec8 = D == 8 && ((reinterpret_cast<uintptr_t>(h.emb) & 31) == 0);  // xs rows are 32-byte aligned
     for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
@@ -573,25 +727,47 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const long long first = (long long)(c - e.chunk_off) * kChunk;
         const long long rem = (long long)e.n - first;
         const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
-        for (int i = threadIdx.x; i < np; i += kPtThreads) {
-            const long long p = e.pt_off + first + i;
-            const unsigned cid = st.key[p];
-            const long long pos = (long long)st.cell_start[cell_off + cid] + st.rank[p];
-            st.perm[pos] = (int)(first + i);
-            st.cell_s[pos] = cid;
-            const float* x = h.emb + p * D;
-            float4* dst = reinterpret_cast<float4*>(st.xs + pos * dp);
-            if (vec) {
-                const float4* src = reinterpret_cast<const float4*>(x);
-                for (int t = 0; t < dp / 4; ++t) dst[t] = __ldg(src + t);
+        for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
+            unsigned cid[kPtBatch], rk[kPtBatch];
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u) {
+                const int i = i0 + u * kPtThreads;
+                const long long p = e.pt_off + first + (i < np ? i : 0);
+                cid[u] = __ldg(st.key + p);
+                rk[u] = __ldg(st.rank + p);
+            }
+            long long pos[kPtBatch];
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u) pos[u] = (long long)__ldg(st.cell_start + cell_off + cid[u]) + rk[u];
+            if (vec8) {
+                // D = 8 (rows of 32 bytes, the input 32-byte aligned): one
+                // 32-byte load and store per row, all loads before any store
+                F8 row[kPtBatch];
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
+                }
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    if (i < np) st_f8(st.xs + pos[u] * 8, row[u]);
+                }
             } else {
-                for (int t = 0; t < dp; t += 4) {
-                    float4 w;
-                    w.x = (t + 0 < D) ? __ldg(x + t + 0) : 0.f;
-                    w.y = (t + 1 < D) ? __ldg(x + t + 1) : 0.f;
-                    w.z = (t + 2 < D) ? __ldg(x + t + 2) : 0.f;
-                    w.w = (t + 3 < D) ? __ldg(x + t + 3) : 0.f;
-                    dst[t / 4] = w;
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    if (i < np)
+                        copy_row(h.emb + (e.pt_off + first + i) * D, reinterpret_cast<float4*>(st.xs + pos[u] * dp), D,
+                                 dp, vec);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPtBatch; ++u) {
+                const int i = i0 + u * kPtThreads;
+                if (i < np) {
+                    st.perm[pos[u]] = (int)(first + i);
+                    st.cell_s[pos[u]] = cid[u];
                 }
             }
         }
