@@ -303,7 +303,7 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     const unsigned long long tiles_c = (unsigned long long)(cells_max + kScanTile - 1) / kScanTile + 1;
     const unsigned long long tiles_r = (n + kRowScanTile - 1) / kRowScanTile + 1;
     const bool d2 = (q.flags & FRNN_EMIT_D2) != 0;
-    unsigned long long b = sizeof(CallHdr) + sizeof(EvDesc) * ev + sizeof(EvPlan) * ev;
+    unsigned long long b = sizeof(CallHdr) + sizeof(EvDesc) * ev + sizeof(EvPlan) * ev + sizeof(int2) * kMaxRuns * ev;
     b += 2 * sizeof(unsigned) * ev * kMaxDims + 2 * sizeof(unsigned) * ev + sizeof(unsigned) * kCtrCount + 4;
     b += 4 * sizeof(unsigned) * n + sizeof(float) * n * dp + 2 * sizeof(int) * n + sizeof(int) * (n + 1);
     b += sizeof(unsigned) * (unsigned long long)cells_max + sizeof(int) * ((unsigned long long)cells_max + 1);
@@ -379,6 +379,7 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     st.hdr = reinterpret_cast<const CallHdr*>(p->d_call);
     st.ev = reinterpret_cast<const EvDesc*>(p->d_call + sizeof(CallHdr));
     ALLOC(st.plan, ev);
+    ALLOC(st.run_tab, ev * kMaxRuns);
     ALLOC(st.bb_min, ev * kMaxDims);
     ALLOC(st.bb_max, ev * kMaxDims);
     ALLOC(st.chunk_done, ev);

@@ -6,6 +6,7 @@
 namespace frnn {
 
 constexpr int kMaxG = 6;            // most gridded dimensions (3^(g-1) runs per cell)
+constexpr int kMaxRuns = 243;       // 3^(kMaxG - 1)
 constexpr int kMaxDims = 64;        // largest embedding dimension
 constexpr int kChunk = 2048;        // points per chunk of the per-point kernels
 constexpr int kPtThreads = 256;     // threads of the per-point kernels
@@ -74,6 +75,7 @@ struct DevState {
     const CallHdr* hdr;
     const EvDesc* ev;
     EvPlan* plan;
+    int2* run_tab;           // [events_max * kMaxRuns] per event and run: cell offset, off-grid dim masks
     unsigned* bb_min;        // [events_max * kMaxDims] order-preserving encodings
     unsigned* bb_max;
     unsigned* chunk_done;    // [events_max]

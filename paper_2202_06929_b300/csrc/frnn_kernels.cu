@@ -137,6 +137,7 @@ __device__ void plan_event(const DevState& st, const CallHdr& h, int b, const Ev
 {
     __shared__ float s_w[kMaxDims];
     __shared__ float s_lo[kMaxDims];
+    __shared__ int s_runs;
     const int D = h.d;
     for (int t = threadIdx.x; t < D; t += blockDim.x) {
         const float lo = ord2f(__ldcg(&st.bb_min[b * kMaxDims + t]));
@@ -198,8 +199,27 @@ __device__ void plan_event(const DevState& st, const CallHdr& h, int b, const Ev
             pl.inv_s = 1.0f / s;
         }
         st.plan[b] = pl;
+        s_runs = pl.g;
     }
     __syncthreads();
+    // the event's runs: run ri takes the offset (digit t of ri in base 3) - 1
+    // along slower dim t; its entry holds the cell offset and the dims with
+    // digit 0 (bits 0..4) and digit 2 (bits 5..9)
+    {
+        const int g = s_runs;
+        const int nr = g >= 6 ? 243 : g == 5 ? 81 : g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
+        for (int ri = threadIdx.x; ri < nr; ri += blockDim.x) {
+            int rem = ri, off = 0, masks = 0;
+            for (int t = 0; t < g - 1; ++t) {
+                const int dgt = rem % 3;
+                off += (dgt - 1) * st.plan[b].stride[t];
+                if (dgt == 0) masks |= 1 << t;
+                if (dgt == 2) masks |= 1 << (5 + t);
+                rem /= 3;
+            }
+            st.run_tab[(size_t)b * kMaxRuns + ri] = make_int2(off, masks);
+        }
+    }
     // leave the per-event accumulators ready for the next build
     for (int t = threadIdx.x; t < D; t += blockDim.x) {
         st.bb_min[b * kMaxDims + t] = 0xffffffffu;
@@ -896,6 +916,11 @@ struct WarpWalk {
     int2 stage[32];
 };
 
+__device__ __forceinline__ int n_runs(int g)
+{
+    return g >= 6 ? 243 : g == 5 ? 81 : g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
+}
+
 __device__ __forceinline__ void load_plan(WarpWalk& ww, const EvPlan* plan, int b, int lane)
 {
     __syncwarp();
@@ -971,30 +996,61 @@ __device__ __forceinline__ Runs make_runs(int beg, int len, int lane)
     return r;
 }
 
-__device__ __forceinline__ int n_runs(int g)
-{
-    return g >= 6 ? 243 : g == 5 ? 81 : g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
-}
-
 // Calls body(Runs) for the segment's runs, in groups of at most 32.  With at
 // most 32 runs (g <= 4) the runs go to the lanes as they are; with more,
 // they are generated 32 at a time and only the non-empty ones are packed
-// into the lanes (at g = 5 or 6 most of the 81 or 243 runs are empty).
+// into the lanes (at g = 5 or 6 most of the 81 or 243 runs are empty).  The
+// many-run case takes each run's cell offset from the event's run table
+// (run_tab[ri] = {offset, slower dims with digit 0 | dims with digit 2 << 5};
+// a run that would step off the grid is dropped by one mask test) and issues
+// the next round's cell-table loads before packing the current round.
 template <typename Body>
-__device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int* cell_start, int lane, Body&& body)
+__device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int2* run_tab, const int* cell_start,
+                                                   int lane, Body&& body)
 {
-    const int nr = n_runs(ww.pl.g);
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const EvPlan& pl = ww.pl;
+    const int g = pl.g;
+    const int nr = n_runs(g);
     if (nr <= 32) {
         int beg = 0, len = 0;
         if (lane < nr) run_of(ww, lane, cell_start, beg, len);
         if (__ballot_sync(kFull, len > 0)) body(make_runs(beg, len, lane));
         return;
     }
+    // the segment's cell: base index of the run with zero offsets along the
+    // slower dims, and the slower dims along which it lies on the grid's
+    // lower (bit t) or upper (bit 5 + t) face
+    int cb = 0, bad = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxG - 1; ++t) {
+        if (t < g - 1) {
+            const int kt = ww.ks[t];
+            cb += kt * pl.stride[t];
+            if (kt == 0) bad |= 1 << t;
+            if (kt == pl.ncell[t] - 1) bad |= 1 << (5 + t);
+        }
+    }
+    const int kl = ww.ks[g - 1], ncl = pl.ncell[g - 1];
+    const int* cs_lo = cell_start + pl.cell_off + cb + max(kl - 1, 0);
+    const int* cs_hi = cell_start + pl.cell_off + cb + min(kl + 1, ncl - 1) + 1;
+    auto run = [&](int ri, int& beg, int& len) {
+        beg = 0;
+        len = 0;
+        if (ri < nr) {
+            const int2 rt = __ldg(run_tab + ri);
+            if ((rt.y & bad) == 0) {
+                beg = __ldg(cs_lo + rt.x);
+                len = __ldg(cs_hi + rt.x) - beg;
+            }
+        }
+    };
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int beg, len;
+    run(lane, beg, len);
     int cnt = 0, gbeg = 0, glen = 0;
     for (int r0 = 0; r0 < nr; r0 += 32) {
-        int beg = 0, len = 0;
-        if (r0 + lane < nr) run_of(ww, r0 + lane, cell_start, beg, len);
+        int nbeg = 0, nlen = 0;
+        if (r0 + 32 < nr) run(r0 + 32 + lane, nbeg, nlen);  // next round, in flight meanwhile
         const unsigned m = __ballot_sync(kFull, len > 0);
         const int nne = __popc(m);
         if (cnt + nne > 32) {
@@ -1012,6 +1068,8 @@ __device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int* cell
         }
         __syncwarp();
         cnt += nne;
+        beg = nbeg;
+        len = nlen;
     }
     if (cnt > 0) body(make_runs(gbeg, glen, lane));
 }
@@ -1166,7 +1224,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
             if (ww.pl.skip) continue;
             segment_cell(ww, sq + (a >> 1) * (2 * DP), a & 1, lane);
             const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
-            for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
+            for_each_run_group(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
                 CandPk<DP4> cp;
@@ -1310,10 +1368,11 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
         const float* qrow = sq;
         const int half = 0;
         segment_cell(ww, qrow, half, lane);
+        const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
         if (K == 0x7fffffff) {
             // no cap: the whole row, written in candidate order
             int nw = 0;
-            for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
+            for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
                 float d2 = 0.f;
@@ -1335,7 +1394,7 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
         }
         unsigned long long thr = ~0ull;
         int nk = 0;
-        for_each_run_group(ww, st.cell_start, lane, [&](const Runs& rn) {
+        for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
         for (int base = 0; base < rn.total; base += 32) {
             const int cand = candidate_at(rn, base + lane);
             unsigned long long key = ~0ull;

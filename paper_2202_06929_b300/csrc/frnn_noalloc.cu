@@ -43,7 +43,8 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffHdr = 0;
 constexpr size_t kOffEv = align256(kOffHdr + sizeof(CallHdr));
 constexpr size_t kOffPlan = align256(kOffEv + sizeof(EvDesc));
-constexpr size_t kOffBbMin = align256(kOffPlan + sizeof(EvPlan));
+constexpr size_t kOffRunOff = align256(kOffPlan + sizeof(EvPlan));
+constexpr size_t kOffBbMin = align256(kOffRunOff + sizeof(int2) * kMaxRuns);
 constexpr size_t kOffBbMax = align256(kOffBbMin + sizeof(unsigned) * kMaxDims);
 constexpr size_t kOffChunkDone = align256(kOffBbMax + sizeof(unsigned) * kMaxDims);
 constexpr size_t kOffNonfinite = align256(kOffChunkDone + sizeof(unsigned));
@@ -163,6 +164,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     st.hdr = reinterpret_cast<const CallHdr*>(b + kOffHdr);
     st.ev = reinterpret_cast<const EvDesc*>(b + kOffEv);
     st.plan = reinterpret_cast<EvPlan*>(b + kOffPlan);
+    st.run_tab = reinterpret_cast<int2*>(b + kOffRunOff);
     st.bb_min = reinterpret_cast<unsigned*>(b + kOffBbMin);
     st.bb_max = reinterpret_cast<unsigned*>(b + kOffBbMax);
     st.chunk_done = reinterpret_cast<unsigned*>(b + kOffChunkDone);
