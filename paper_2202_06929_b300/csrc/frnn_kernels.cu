@@ -676,11 +676,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         out[M] = (int)last_incl;
         *tile_ctr = 0u;
         *exit_ctr = 0u;
-        if (MODE == 0) st.counters[kCtrLongRows] = 0u;  // the emit walk of the last build is done with it
+        if (MODE == 0) {  // the emit walk of the last build is done with both
+            st.counters[kCtrLongRows] = 0u;
+            st.counters[kCtrEmitRows] = 0u;
+        }
     }
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
     if (MODE == 1) {
-        if (threadIdx.x == 0) *st.pool_ctr = 0ull;  // the collect walk is done with it
+        if (threadIdx.x == 0) {
+            *st.pool_ctr = 0ull;                  // the collect walk is done with both
+            st.counters[kCtrWalkChunks] = 0u;
+        }
         // per-event edge offsets, and the capacity check of the emit walk
         const int B = st.hdr->n_events;
         for (int b = threadIdx.x; b <= B; b += blockDim.x) {
@@ -1164,6 +1170,7 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
 // slot per query in shared memory) and sorted there; longer rows are left to
 // the emit walk, which selects the k smallest keys on its own.
 constexpr int kFast = 24;
+constexpr int kChunkGroup = 2;  // consecutive chunks a warp takes at a time
 constexpr int kRowSlots = kFast + 1;   // a row also holds the query's own key while collecting
 constexpr int kRowStride = kFast + 1;  // = kRowSlots; odd, so row starts of lanes 0..15 fall in distinct banks
 
@@ -1195,7 +1202,6 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     const int emit = st.hdr->emit_d2;
     const long long pool_cap = st.hdr->edge_capacity;
     const long long nchunks = (P + 31) >> 5;
-    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
     LaneEvent le;
     le.lo = 1;
@@ -1203,7 +1209,16 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     __shared__ WarpWalk s_ww[kWalkThreads / 32];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    for (long long ch = (long long)blockIdx.x * (kWalkThreads / 32) + wib; ch < nchunks; ch += nwarps) {
+    // Warps take runs of kChunkGroup consecutive chunks from a counter: the
+    // chunks of a run mostly share an event (its plan and the lanes' event
+    // lookups carry over) and neighbouring cells (candidates stay in L1).
+    for (;;) {
+    unsigned g0 = 0;
+    if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], (unsigned)kChunkGroup);
+    g0 = __shfl_sync(kFull, g0, 0);
+    if ((long long)g0 >= nchunks) break;
+    const long long gend = min((long long)g0 + kChunkGroup, nchunks);
+    for (long long ch = g0; ch < gend; ++ch) {
         const long long q0 = ch << 5;
         const long long q = q0 + lane;
         const bool valid = q < P;
@@ -1316,6 +1331,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
         }
         __syncwarp();
     }
+    }
 }
 
 // Stage 7: the long rows (more than kFast neighbours, or no pool space), one
@@ -1338,12 +1354,16 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     const int emit = st.hdr->emit_d2;
     const long long ecap = st.hdr->edge_capacity;
     const int n_long = (int)st.counters[kCtrLongRows];
-    const int nwarps = gridDim.x * (kFillThreads / 32);
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
     __shared__ WarpWalk s_ww[kFillThreads / 32];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    for (int li = blockIdx.x * (kFillThreads / 32) + wib; li < n_long; li += nwarps) {
+    // rows are taken one at a time from a counter (their costs vary widely)
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = (int)atomicAdd(&st.counters[kCtrEmitRows], 1u);
+        li = __shfl_sync(kFull, li, 0);
+        if (li >= n_long) break;
         const long long q = (long long)st.rank[li];
         const int b = event_of_point(st.ev, B, q);
         const long long p = st.ev[b].pt_off + __ldg(st.perm + q);
