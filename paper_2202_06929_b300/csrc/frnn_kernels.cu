@@ -1212,12 +1212,16 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     // Warps take runs of kChunkGroup consecutive chunks from a counter: the
     // chunks of a run mostly share an event (its plan and the lanes' event
     // lookups carry over) and neighbouring cells (candidates stay in L1).
+    // (one chunk at a time when there are few chunks per warp, so that small
+    // builds still spread over every warp)
+    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const unsigned group = nchunks >= 4 * nwarps ? (unsigned)kChunkGroup : 1u;
     for (;;) {
     unsigned g0 = 0;
-    if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], (unsigned)kChunkGroup);
+    if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], group);
     g0 = __shfl_sync(kFull, g0, 0);
     if ((long long)g0 >= nchunks) break;
-    const long long gend = min((long long)g0 + kChunkGroup, nchunks);
+    const long long gend = min((long long)g0 + group, nchunks);
     for (long long ch = g0; ch < gend; ++ch) {
         const long long q0 = ch << 5;
         const long long q = q0 + lane;
