@@ -49,7 +49,7 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM read + write bytes per point of the collect walk, from the ncu capture
 # summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
 # kernel source it was taken on (traffic scales with the points processed).
-MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "04fe1fa2c75d", "bytes_per_point": 446_506_752 / 4_800_000}
+MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b90da92e8002", "bytes_per_point": 439_689_472 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -221,9 +221,12 @@ def stage_bytes(n_total: int, n_edges: int, d: int):
         "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total,
         # sorted points read once; per point its cell id, count and pool slot; rows parked
         "walk_collect": 4 * n_total * dp + 4 * n_total + 8 * n_total + 4 * n_edges,
-        "scan_rows": 8 * n_total,
-        # per point perm, pool slot and row_ptr; rows read from the pool and written to col
-        "walk_emit": 8 * n_total + 4 * (n_total + 1) + 8 * n_edges,
+        # per point its count and pool slot read, row_ptr written; parked rows
+        # read from the pool and written to col
+        "scan_rows": 12 * n_total + 8 * n_edges,
+        # only the rows longer than the collect walk keeps (none on the C2
+        # workload): not counted
+        "walk_emit": 0,
     }
 
 
