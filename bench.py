@@ -49,6 +49,7 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM read + write bytes per point of the collect walk, from the ncu capture
 # summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
 # kernel source it was taken on (traffic scales with the points processed).
+KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b90da92e8002", "bytes_per_point": 439_689_472 / 4_800_000}
 
 
@@ -230,6 +231,54 @@ def stage_bytes(n_total: int, n_edges: int, d: int):
     }
 
 
+def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point: int, sample: int = 100_000,
+                    seed: int = 3):
+    """Mean number of candidates a query of this event is tested against by
+    the walk (the points of the 3^g cells around its cell), recounted on the
+    host with the planning rule (widest dims first, cell edge
+    r * cell_scale * (1 + 2^-6), stop below 4 cells or over the cell budget),
+    over a random sample of queries."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, dd = x.shape
+    lo = x.min(0)
+    w = (x.max(0) - lo).astype(np.float32)
+    order = np.argsort(-w, kind="stable")
+    npick = min(g_max or 4, 6, dd)
+    s = np.float32(r) * np.float32(cell_scale or 1.0) * np.float32(1 + 1 / 64)
+    budget = cells_per_point * n + 4096
+    maxc0 = min(budget, 32768)
+    if w[order[0]] / s > maxc0 - 3:
+        s = np.float32(w[order[0]] / np.float32(maxc0 - 3) * np.float32(1 + 1 / 64))
+    dims, ncs, cells = [], [], 1
+    for i in range(npick):
+        t = int(order[i])
+        a = w[t] / s
+        nc = 32768 if a >= 32767 else int(a) + 1
+        if dims and (nc < 4 or cells * nc > budget):
+            break
+        dims.append(t)
+        ncs.append(nc)
+        cells *= nc
+    ncs = np.array(ncs)
+    inv_s = np.float32(1) / s
+    k = np.minimum(((x[:, dims] - lo[dims]) * inv_s).astype(np.int64), ncs - 1)
+    cid = np.ravel_multi_index(k.T, ncs)
+    start = np.concatenate([[0], np.cumsum(np.bincount(cid, minlength=int(np.prod(ncs))))])
+    q = np.random.default_rng(seed).choice(n, size=min(sample, n), replace=False)
+    kq = k[q]
+    g = len(dims)
+    tot = np.zeros(len(q), np.int64)
+    import itertools
+    for offs in itertools.product((-1, 0, 1), repeat=g - 1):
+        kk = kq[:, :g - 1] + np.array(offs, dtype=np.int64)
+        ok = np.all((kk >= 0) & (kk < ncs[:g - 1]), axis=1)
+        kk = np.clip(kk, 0, ncs[:g - 1] - 1)
+        c0 = np.ravel_multi_index(np.concatenate([kk, np.maximum(kq[:, g - 1:] - 1, 0)], 1).T, ncs)
+        c1 = np.ravel_multi_index(np.concatenate([kk, np.minimum(kq[:, g - 1:] + 1, ncs[g - 1] - 1)], 1).T, ncs)
+        tot += np.where(ok, start[c1 + 1] - start[c0], 0)
+    return float(tot.mean()), g
+
+
 # --------------------------------------------------------------------------- CPU oracle
 
 def run_cpu_baseline(x, queries: int, seed: int = 0, r: float = R, k: int = K):
@@ -242,6 +291,30 @@ def run_cpu_baseline(x, queries: int, seed: int = 0, r: float = R, k: int = K):
     return {"value": (len(q) / n) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{len(q)} random query rows of one N={n} event (brute force over all {n} points), "
                       f"{dt:.2f} s; events/s = (rows / N) / s"}
+
+
+def run_cpu_single_core(x, queries: int, seed: int = 7, r: float = R, k: int = K):
+    """The same oracle on one host core (OMP_NUM_THREADS=1, in a child process
+    so that this process's OpenMP runtime keeps its thread count)."""
+    import subprocess
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "event.npy")
+        np.save(path, np.ascontiguousarray(x, dtype=np.float32))
+        code = ("import json, sys, time; import numpy as np; sys.path.insert(0, {root!r}); import oracle; "
+                "x = np.load({path!r}); n = x.shape[0]; "
+                "q = np.random.default_rng({seed}).choice(n, size=min({queries}, n), replace=False); "
+                "t0 = time.perf_counter(); oracle.radius_graph(x, {r!r}, {k}, queries=q); "
+                "dt = time.perf_counter() - t0; "
+                "print(json.dumps({{'rows': int(len(q)), 'n': int(n), 's': dt, 'threads': oracle.num_threads()}}))"
+                ).format(root=ROOT, path=path, seed=seed, queries=int(queries), r=float(r), k=int(k))
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        return {"error": res.stderr.strip().splitlines()[-1] if res.stderr.strip() else f"exit {res.returncode}"}
+    o = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": (o["rows"] / o["n"]) / o["s"], "unit": UNIT, "cores": o["threads"],
+            "sample": f"{o['rows']} random query rows of the same event, {o['s']:.2f} s on one core"}
 
 
 def reference_arm(args, rank, world):
@@ -492,8 +565,34 @@ def main(argv=None):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(x_host[off[0]:off[1]], args.cpu_queries, r=r, k=k)
+        cpu["single_core"] = run_cpu_single_core(x_host[off[0]:off[1]], max(args.cpu_queries // 16, 100), r=r, k=k)
 
     clocks = clk.summary()
+    # ---- arithmetic view of the walks: candidate distance tests per step
+    # (every query against its candidates in the collect walk, and the long
+    # rows once more in the emit walk), FP32 operations 3 D per test (one
+    # subtraction, one product, one addition per dim), against the FP32 rate
+    # derived from the SM count, 128 FP32 lanes per SM, two operations per
+    # lane per packed f32x2 instruction, and the maximum SM clock
+    alu = None
+    if rank == 0:
+        g_used, s_used = plan.get_tuning()
+        mean_cand, g_grid = host_candidates(x_host[off[0]:off[1]], r, g_used, s_used, cpp)
+        row_len = np.diff(plan.build_batched(x_dev, off, r, k, stream=stream).to_host()["row_ptr"].astype(np.int64))
+        torch.cuda.synchronize(dev)
+        long_frac = float(np.mean(row_len > KFAST_ROWS))
+        evals = mean_cand * n_total * (1.0 + long_frac)
+        ops = evals * 3 * d
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_tops = n_sm * 128 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks["sm_max_mhz"] else None
+        achieved_tops = ops / (total_ms_max / args.steps / 1e3) / 1e12
+        alu = {"candidate_tests_per_step": evals, "mean_candidates_per_query": mean_cand,
+               "gridded_dims": g_grid, "long_row_fraction": long_frac,
+               "candidate_tests_per_s": evals / (total_ms_max / args.steps / 1e3),
+               "fp32_ops_per_test": 3 * d, "achieved_tops": achieved_tops, "peak_tops_derived": peak_tops,
+               "frac": achieved_tops / peak_tops if peak_tops else None,
+               "note": "candidates recounted on the host (event 0, 100k sampled queries, the plan's grid rule); "
+                       "peak = SMs x 128 FP32 lanes x 2 (packed f32x2) x max SM clock, derived, not measured"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -527,7 +626,8 @@ def main(argv=None):
                          "launch_ms": stage_avg[dom],
                          "whole_build": {"algorithmic_bytes": whole_bytes,
                                          "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
-                                         "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak}},
+                                         "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak},
+                         "alu_view": alu},
             "e2e": e2e,
             "labeling": labeling,
             "served": served,

@@ -66,7 +66,7 @@ struct EvPlan {
 
 // Counter slots (all return to zero at the end of every build).
 enum { kCtrPlanned = 0, kCtrScanCellsTile, kCtrScanCellsExit, kCtrScanRowsTile,
-       kCtrScanRowsExit, kCtrLongRows, kCtrWalkChunks, kCtrEmitRows, kCtrCount = 8 };
+       kCtrScanRowsExit, kCtrLongRows, kCtrWalkChunks, kCtrEmitRows, kCtrLabelCapped, kCtrCount = 16 };
 
 // Device pointers owned by the plan.  Fixed for the plan's life, so a
 // captured CUDA graph of the build stays valid for every call: everything

@@ -8,11 +8,15 @@
 // direction is ignored, and every point gets the smallest index of its
 // component as its label, so labels are unique and independent of timing.
 //
-// Lock-free union-find over a parent array of call-wide point indices: a root
-// is only ever attached (by compare-and-swap) under a smaller root, and path
-// halving only moves a pointer to an ancestor, so every parent pointer is <=
-// its index; finds therefore end after at most `index` steps, and the root of
-// a component is its minimum.
+// Lock-free union-find over a parent array of call-wide point indices, in
+// four passes: every point starts under its smallest kept neighbour; paths
+// are compressed (each point then hangs directly under its root, and on
+// clustered data almost every edge already lies inside one tree); each edge
+// whose ends hang under different roots joins the trees, a root only ever
+// being attached (by compare-and-swap) under a smaller root; the labels are
+// read off.  Every parent pointer is a smaller point of the same component
+// (or the point itself), so finds end, and the root of a component is its
+// minimum.
 #include <cuda_runtime.h>
 
 #include "frnn_internal.h"
@@ -23,7 +27,9 @@ namespace {
 constexpr int kLabelThreads = 256;
 constexpr int kUnionLimit = 1 << 20;  // retries of one union (each failure means another thread progressed)
 
-__device__ __forceinline__ int ld_volatile(const int* p)
+// Parent reads that see other threads' updates (volatile: never cached in a
+// register or in L1).
+__device__ __forceinline__ int ld_parent(const int* p)
 {
     return *reinterpret_cast<const volatile int*>(p);
 }
@@ -31,9 +37,9 @@ __device__ __forceinline__ int ld_volatile(const int* p)
 __device__ __forceinline__ int find_root(int* parent, int x)
 {
     for (;;) {
-        const int px = ld_volatile(parent + x);
+        const int px = ld_parent(parent + x);
         if (px == x) return x;
-        const int ppx = ld_volatile(parent + px);
+        const int ppx = ld_parent(parent + px);
         if (ppx != px) parent[x] = ppx;  // path halving: ppx is an ancestor of x
         x = ppx;
     }
@@ -67,15 +73,14 @@ __device__ __forceinline__ int event_of(const EvDesc* ev, int n_events, long lon
     return lo;
 }
 
-__global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* parent)
+// Start of the forest: every point points at its smallest kept neighbour (or
+// at itself).  A parent is a smaller point of the same component, so this is
+// a valid union-find state, and a cluster whose points are all neighbours of
+// one another is already a one-level tree.
+__global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* parent, float d2_max, int use_d2)
 {
-    const long long P = st.hdr->n_total;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
-        parent[p] = (int)p;
-}
-
-__global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int* parent, float d2_max, int use_d2)
-{
+    unsigned* capped = &st.counters[kCtrLabelCapped];
+    const int K = st.hdr->k;
     const long long P = st.hdr->n_total;
     const int B = st.hdr->n_events;
     const long long ecap = st.hdr->edge_capacity;
@@ -88,10 +93,72 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int*
             hi = off + st.ev[b].n;
         }
         const int rs = st.row_ptr[p], re = st.row_ptr[p + 1];
+        long long m = p;
+        if ((long long)re <= ecap) {
+            for (int e = rs; e < re; ++e) {
+                if (use_d2 && !(st.d2[e] <= d2_max)) continue;
+                m = min(m, off + st.col[e]);
+            }
+        }
+        parent[p] = (int)m;
+        // a row of k entries may have been cut at k: note it for the union pass
+        if (re - rs >= K) atomicOr(capped, 1u);
+    }
+}
+
+// Full path compression after the start: every point is made to point at its
+// root (reads along the chain; the one write only shortens a path, which is
+// safe while other threads walk it).
+__global__ void __launch_bounds__(kLabelThreads) k_label_compress(DevState st, int* parent)
+{
+    const long long P = st.hdr->n_total;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        int x = parent[p];
+        if (x == (int)p) continue;
+        int px = ld_parent(parent + x);
+        while (px != x) {
+            x = px;
+            px = ld_parent(parent + x);
+        }
+        parent[p] = x;
+    }
+}
+
+// Every kept edge joins its two trees.  An edge p -> q with q < p is left to
+// q's row when that row holds all of q's neighbours (it was not cut at k),
+// since q -> p is then processed from there (when no row of the build was
+// cut, that holds for every such edge).  p's root is carried from edge to
+// edge (a root that was hooked meanwhile is still an ancestor of p), and an
+// edge whose far end already hangs directly under it costs one load.
+__global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int* parent, float d2_max, int use_d2)
+{
+    const bool any_capped = __ldcg(&st.counters[kCtrLabelCapped]) != 0u;
+    const long long P = st.hdr->n_total;
+    const int B = st.hdr->n_events;
+    const int K = st.hdr->k;
+    const long long ecap = st.hdr->edge_capacity;
+    long long lo = 1, hi = 0, off = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        if (p < lo || p >= hi) {
+            const int b = event_of(st.ev, B, p);
+            off = st.ev[b].pt_off;
+            lo = off;
+            hi = off + st.ev[b].n;
+        }
+        const int rs = st.row_ptr[p], re = st.row_ptr[p + 1];
         if ((long long)re > ecap) continue;  // rows past the edge capacity were never written
+        int rp = -1;
         for (int e = rs; e < re; ++e) {
             if (use_d2 && !(st.d2[e] <= d2_max)) continue;
-            if (!unite(parent, (int)p, (int)(off + st.col[e]))) atomicOr(st.status, kStTimeout);
+            const long long q = off + st.col[e];
+            if (q < p && (!any_capped || st.cnt_o[q] < K)) continue;
+            if (rp < 0) rp = __ldcg(parent + p);  // an ancestor of p (its root after compression)
+            const int pq = __ldcg(parent + q);
+            if (pq == rp) continue;  // q's parent is p's root (trees only merge)
+            const int rq = find_root(parent, pq);
+            if (rq == rp) continue;
+            if (!unite(parent, rp, rq)) atomicOr(st.status, kStTimeout);
+            rp = find_root(parent, rp);
         }
     }
 }
@@ -110,6 +177,7 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_final(DevState st, int*
         }
         labels[p] = (int)(find_root(parent, (int)p) - off);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st.counters[kCtrLabelCapped] = 0u;  // read by the union pass only
 }
 
 }  // namespace
@@ -117,7 +185,8 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_final(DevState st, int*
 int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int use_d2, int grid, void* stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    k_label_init<<<grid, kLabelThreads, 0, s>>>(st, parent);
+    k_label_init<<<grid, kLabelThreads, 0, s>>>(st, parent, d2_max, use_d2);
+    k_label_compress<<<grid, kLabelThreads, 0, s>>>(st, parent);
     k_label_union<<<grid, kLabelThreads, 0, s>>>(st, parent, d2_max, use_d2);
     k_label_final<<<grid, kLabelThreads, 0, s>>>(st, parent, labels);
     return (int)cudaGetLastError();
