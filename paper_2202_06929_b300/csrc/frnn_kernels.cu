@@ -880,24 +880,6 @@ __device__ __forceinline__ float2 dist2_pair(const ulonglong2* qp, const CandPk<
     return make_float2(__uint_as_float((unsigned)s), __uint_as_float((unsigned)(s >> 32)));
 }
 
-// Scalar form for one query (slow path of the fill walk).
-template <int DP4>
-__device__ __forceinline__ float dist2_one(const float* qrow /* smem, interleaved */, int half,
-                                           const float4* crow)
-{
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < DP4; ++k) {
-        const float4 v = __ldg(crow + k);
-        float d;
-        d = __fsub_rn(qrow[2 * (4 * k + 0) + half], v.x); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(qrow[2 * (4 * k + 1) + half], v.y); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(qrow[2 * (4 * k + 2) + half], v.z); s = __fadd_rn(s, __fmul_rn(d, d));
-        d = __fsub_rn(qrow[2 * (4 * k + 3) + half], v.w); s = __fadd_rn(s, __fmul_rn(d, d));
-    }
-    return s;
-}
-
 // Per-lane cache of the lane's event.
 struct LaneEvent {
     long long lo, hi, pt_off;
@@ -1338,9 +1320,36 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
     }
 }
 
-// Stage 7: the long rows (more than kFast neighbours, or no pool space), one
-// warp per row from the collect walk's list: walk the row's cell runs again
-// and keep the k smallest keys (or, with no cap, every neighbour).
+// Sorted output of one long row: the smallest min(cnt, nk) of its nk keys.
+__device__ __forceinline__ void emit_row_out(const DevState& st, unsigned long long* keys, int nk, int rsi, int cnt,
+                                             int emit, int lane)
+{
+    const int nout = min(cnt, nk);
+    if (nk <= 32) {
+        unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
+        v = warp_sort32(v, lane);
+        if (lane < nout) {
+            st.col[rsi + lane] = (int)(unsigned)v;
+            if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
+        }
+    } else {
+        warp_sort_smem(keys, nk, lane);
+        for (int e2 = lane; e2 < nout; e2 += 32) {
+            const unsigned long long v = keys[e2];
+            st.col[rsi + e2] = (int)(unsigned)v;
+            if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
+        }
+    }
+    __syncwarp();
+}
+
+// Stage 7: the long rows (more than kFast neighbours, or no pool space), from
+// the collect walk's list.  A warp takes two consecutive entries; when both
+// queries lie in the same cell of the same event (the list follows the cell
+// order, so they usually do) it walks their common candidates once, two
+// queries per packed operation, otherwise one query at a time.  Each row
+// keeps its k smallest keys in its own buffer of `cap` keys with a running
+// threshold (with no cap: every neighbour, written in candidate order).
 template <int DP4>
 __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(DevState st, int cap)
 {
@@ -1348,9 +1357,11 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (2 * DP);
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(
-        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (2 * DP)) + (size_t)wib * cap;
+    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (2 * DP);  // one pair row: q0[t], q1[t] interleaved
+    const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
+    unsigned long long* keys0 = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (2 * DP)) + (size_t)wib * 2 * cap;
+    unsigned long long* keys1 = keys0 + cap;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float r2 = st.hdr->r2;
     const int K = st.hdr->k;
@@ -1362,106 +1373,129 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     __shared__ WarpWalk s_ww[kFillThreads / 32];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    // rows are taken one at a time from a counter (their costs vary widely)
+    // two list entries at a time from a counter (row costs vary widely)
     for (;;) {
         int li = 0;
-        if (lane == 0) li = (int)atomicAdd(&st.counters[kCtrEmitRows], 1u);
+        if (lane == 0) li = (int)atomicAdd(&st.counters[kCtrEmitRows], 2u);
         li = __shfl_sync(kFull, li, 0);
         if (li >= n_long) break;
-        const long long q = (long long)st.rank[li];
-        const int b = event_of_point(st.ev, B, q);
-        const long long p = st.ev[b].pt_off + __ldg(st.perm + q);
-        const int rsi = st.row_ptr[p];
-        const int re = st.row_ptr[p + 1];
-        if ((long long)re > ecap) continue;  // over capacity: OVERFLOW already latched
-        const int cnti = re - rsi;
-        // the query's coordinates, in slot 0 of a pair row
-        __syncwarp();
-        if (lane < DP4) {
-            const float4 v = __ldg(xs4 + q * DP4 + lane);
-            sq[2 * (4 * lane + 0)] = v.x;
-            sq[2 * (4 * lane + 1)] = v.y;
-            sq[2 * (4 * lane + 2)] = v.z;
-            sq[2 * (4 * lane + 3)] = v.w;
-        }
-        __syncwarp();
-        if (b != plan_b) {
-            load_plan(ww, st.plan, b, lane);
-            plan_b = b;
-        }
-        const float* qrow = sq;
-        const int half = 0;
-        segment_cell(ww, qrow, half, lane);
-        const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
-        if (K == 0x7fffffff) {
-            // no cap: the whole row, written in candidate order
-            int nw = 0;
+        const long long qa = (long long)st.rank[li];
+        const long long qb = li + 1 < n_long ? (long long)st.rank[li + 1] : -1;
+        const int ba = event_of_point(st.ev, B, qa);
+        const bool together = qb >= 0 && __ldg(st.cell_s + qa) == __ldg(st.cell_s + qb) &&
+                              event_of_point(st.ev, B, qb) == ba;
+        // one or two passes: (qa, qb) together, or qa then qb
+        for (int pass = 0; pass < (together || qb < 0 ? 1 : 2); ++pass) {
+            const long long q0 = pass == 0 ? qa : qb;
+            const long long q1 = together ? qb : -1;
+            const int b = pass == 0 ? ba : event_of_point(st.ev, B, q0);
+            const long long pt = st.ev[b].pt_off;
+            int rs0 = 0, cnt0 = 0, rs1 = 0, cnt1 = 0;
+            bool on0, on1 = false;
+            {
+                const long long p = pt + __ldg(st.perm + q0);
+                rs0 = st.row_ptr[p];
+                const int re = st.row_ptr[p + 1];
+                on0 = (long long)re <= ecap;  // over capacity: OVERFLOW already latched
+                cnt0 = re - rs0;
+            }
+            if (q1 >= 0) {
+                const long long p = pt + __ldg(st.perm + q1);
+                rs1 = st.row_ptr[p];
+                const int re = st.row_ptr[p + 1];
+                on1 = (long long)re <= ecap;
+                cnt1 = re - rs1;
+            }
+            if (!on0 && !on1) continue;
+            // the queries' coordinates, interleaved as a pair row (the second
+            // slot repeats the first when the warp walks one query)
+            __syncwarp();
+            if (lane < DP4) {
+                const float4 v = __ldg(xs4 + q0 * DP4 + lane);
+                const float4 u = q1 >= 0 ? __ldg(xs4 + q1 * DP4 + lane) : v;
+                sq[2 * (4 * lane + 0)] = v.x; sq[2 * (4 * lane + 0) + 1] = u.x;
+                sq[2 * (4 * lane + 1)] = v.y; sq[2 * (4 * lane + 1) + 1] = u.y;
+                sq[2 * (4 * lane + 2)] = v.z; sq[2 * (4 * lane + 2) + 1] = u.z;
+                sq[2 * (4 * lane + 3)] = v.w; sq[2 * (4 * lane + 3) + 1] = u.w;
+            }
+            __syncwarp();
+            if (b != plan_b) {
+                load_plan(ww, st.plan, b, lane);
+                plan_b = b;
+            }
+            segment_cell(ww, sq, 0, lane);
+            const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
+            if (K == 0x7fffffff) {
+                // no cap: whole rows, written in candidate order
+                int nw0 = 0, nw1 = 0;
+                for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    CandPk<DP4> cp;
+                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                    const float2 d = dist2_pair<DP4>(sqp, cp);
+                    const bool t0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                    const bool t1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                    const unsigned m0 = __ballot_sync(kFull, t0);
+                    const unsigned m1 = __ballot_sync(kFull, t1);
+                    if (m0 | m1) {
+                        const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                        const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
+                        if (t0 && s0 < cnt0) {
+                            st.col[rs0 + s0] = j;
+                            if (emit) st.d2[rs0 + s0] = d.x;
+                        }
+                        if (t1 && s1 < cnt1) {
+                            st.col[rs1 + s1] = j;
+                            if (emit) st.d2[rs1 + s1] = d.y;
+                        }
+                        nw0 += __popc(m0);
+                        nw1 += __popc(m1);
+                    }
+                }
+                });
+                continue;
+            }
+            unsigned long long thr0 = ~0ull, thr1 = ~0ull;
+            int nk0 = 0, nk1 = 0;
             for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
             for (int base = 0; base < rn.total; base += 32) {
                 const int cand = candidate_at(rn, base + lane);
-                float d2 = 0.f;
-                bool take = false;
-                if (cand >= 0) {
-                    d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
-                    take = d2 <= r2 && (long long)cand != q;
+                CandPk<DP4> cp;
+                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                const float2 d = dist2_pair<DP4>(sqp, cp);
+                const bool h0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                const bool h1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                if (!__any_sync(kFull, h0 || h1)) continue;
+                const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
+                bool t0 = h0 && k0 < thr0, t1 = h1 && k1 < thr1;
+                unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
+                if (nk0 + 32 > cap && m0) {
+                    // only reached when |S_i| > k: keep the k smallest so far
+                    warp_sort_smem(keys0, nk0, lane);
+                    nk0 = K;
+                    thr0 = keys0[K - 1];
+                    t0 = t0 && k0 < thr0;
+                    m0 = __ballot_sync(kFull, t0);
                 }
-                const unsigned m = __ballot_sync(kFull, take);
-                const int slot = nw + __popc(m & lt_mask);
-                if (take && slot < cnti) {
-                    st.col[rsi + slot] = __ldg(st.perm + cand);
-                    if (emit) st.d2[rsi + slot] = d2;
+                if (nk1 + 32 > cap && m1) {
+                    warp_sort_smem(keys1, nk1, lane);
+                    nk1 = K;
+                    thr1 = keys1[K - 1];
+                    t1 = t1 && k1 < thr1;
+                    m1 = __ballot_sync(kFull, t1);
                 }
-                nw += __popc(m);
+                if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
+                if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
+                nk0 += __popc(m0);
+                nk1 += __popc(m1);
+                __syncwarp();
             }
             });
-            continue;
+            if (on0) emit_row_out(st, keys0, nk0, rs0, cnt0, emit, lane);
+            if (on1) emit_row_out(st, keys1, nk1, rs1, cnt1, emit, lane);
         }
-        unsigned long long thr = ~0ull;
-        int nk = 0;
-        for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
-        for (int base = 0; base < rn.total; base += 32) {
-            const int cand = candidate_at(rn, base + lane);
-            unsigned long long key = ~0ull;
-            bool take = false;
-            if (cand >= 0) {
-                const float d2 = dist2_one<DP4>(qrow, half, xs4 + (long long)cand * DP4);
-                if (d2 <= r2 && (long long)cand != q) {
-                    key = edge_key(d2, __ldg(st.perm + cand));
-                    take = key < thr;
-                }
-            }
-            unsigned m = __ballot_sync(kFull, take);
-            if (m == 0u) continue;
-            if (nk + 32 > cap) {
-                // only reached when |S_i| > k: keep the k smallest so far
-                warp_sort_smem(keys, nk, lane);
-                nk = K;
-                thr = keys[K - 1];
-                take = take && (key < thr);
-                m = __ballot_sync(kFull, take);
-            }
-            if (take) keys[nk + __popc(m & lt_mask)] = key;
-            nk += __popc(m);
-            __syncwarp();
-        }
-        });
-        const int nout = min(cnti, nk);
-        if (nk <= 32) {
-            unsigned long long v = (lane < nk) ? keys[lane] : ~0ull;
-            v = warp_sort32(v, lane);
-            if (lane < nout) {
-                st.col[rsi + lane] = (int)(unsigned)v;
-                if (emit) st.d2[rsi + lane] = __uint_as_float((unsigned)(v >> 32));
-            }
-        } else {
-            warp_sort_smem(keys, nk, lane);
-            for (int e2 = lane; e2 < nout; e2 += 32) {
-                const unsigned long long v = keys[e2];
-                st.col[rsi + e2] = (int)(unsigned)v;
-                if (emit) st.d2[rsi + e2] = __uint_as_float((unsigned)(v >> 32));
-            }
-        }
-        __syncwarp();
     }
 }
 
@@ -1481,7 +1515,7 @@ int collect_smem()
 template <int DP4>
 int emit_smem(int cap)
 {
-    return (kFillThreads / 32) * (2 * 4 * DP4 * (int)sizeof(float) + cap * (int)sizeof(unsigned long long));
+    return (kFillThreads / 32) * (2 * 4 * DP4 * (int)sizeof(float) + 2 * cap * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>
