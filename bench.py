@@ -498,7 +498,7 @@ def main(argv=None):
         n_tracks = int((lab.cpu().numpy() == np.arange(n_total) - np.repeat(off[:-1], np.diff(off))).sum())
         labeling = {"ms_per_step": float(np.median(lab_ms)), "components_per_step": n_tracks,
                     "note": "frnn_label_components: weakly connected components of the step's graphs "
-                            "(all edges kept), 3 kernels, after the build on the same stream"}
+                            "(all edges kept), 4 kernels, after the build on the same stream"}
 
     # ---- per-stage times of the batched build (CUDA events between stages)
     stage_ms = {s: [] for s in STAGES}
