@@ -433,6 +433,9 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_key_hist(DevState st)
 // latches FRNN_ERR_TIMEOUT instead of hanging.  The block that exits last
 // clears the tile states and counters for the next build.
 
+// Longest row the collect walk parks (longer rows go to the emit walk).
+constexpr int kFast = 24;
+
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 
@@ -521,10 +524,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
     // slot and the warp-level prefix of the entries to copy
     constexpr int IT = MODE == 0 ? kScanItems : kRowScanItems;  // items per thread
     constexpr int SUB = kScanThreads * IT;
-    __shared__ int s_rs[MODE == 1 ? SUB : 1];
-    __shared__ int s_po[MODE == 1 ? SUB : 1];
-    __shared__ int s_pre[MODE == 1 ? SUB : 1];
+    // per warp: its copied rows in order (first entry in the warp's list,
+    // pool slot, row start), a bitmap of the entries that start a row, and
+    // the number of row starts before each bitmap word
+    constexpr int WP = 32 * IT;                 // points of a warp
+    constexpr int kWords = (WP * kFast + 31) / 32;
+    constexpr int NW = kScanThreads / 32;
+    __shared__ int s_lpre[MODE == 1 ? NW * WP : 1];
+    __shared__ int s_lsrc[MODE == 1 ? NW * WP : 1];
+    __shared__ int s_ldst[MODE == 1 ? NW * WP : 1];
+    __shared__ unsigned s_bm[MODE == 1 ? NW * kWords : 1];
+    __shared__ int s_wb[MODE == 1 ? NW * kWords : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
     long long M;
     unsigned* in;
     int* out;
@@ -603,42 +615,75 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
                 const long long ecap = st.hdr->edge_capacity;
                 const int emit = st.hdr->emit_d2;
                 unsigned rs = prefix + texcl;
+                bool cp[IT];
+                int c[IT], rsv[IT];
                 int mine = 0;
 #pragma unroll
                 for (int i = 0; i < IT; ++i) {
-                    const int loc = threadIdx.x * IT + i;
-                    const bool cp = base + i < M && v[i] > 0u && (long long)rs + v[i] <= ecap && po[i] >= 0;
-                    s_rs[loc] = (int)rs;
-                    s_po[loc] = po[i];
-                    s_pre[loc] = mine;  // exclusive within the thread for now
-                    mine += cp ? (int)v[i] : 0;
+                    cp[i] = base + i < M && v[i] > 0u && (long long)rs + v[i] <= ecap && po[i] >= 0;
+                    c[i] = cp[i] ? (int)v[i] : 0;  // parked rows hold at most kFast entries
+                    rsv[i] = (int)rs;
+                    mine += c[i];
                     rs += v[i];
                 }
                 const int wexcl = warp_incl_scan(mine, lane) - mine;
                 const int wtot = __shfl_sync(kFull, wexcl + mine, 31);
+                int* lpre = s_lpre + warp * WP;
+                int* lsrc = s_lsrc + warp * WP;
+                int* ldst = s_ldst + warp * WP;
+                unsigned* bm = s_bm + warp * kWords;
+                int* wb = s_wb + warp * kWords;
+                for (int w = lane; w < kWords; w += 32) bm[w] = 0u;
+                // the warp's copied rows, in point order (= order of their entries)
+                unsigned bl[IT];
 #pragma unroll
-                for (int i = 0; i < IT; ++i) s_pre[threadIdx.x * IT + i] += wexcl;
+                for (int i = 0; i < IT; ++i) bl[i] = __ballot_sync(kFull, cp[i]);
+                int before = 0;
+#pragma unroll
+                for (int i = 0; i < IT; ++i) before += __popc(bl[i] & lt_mask);
                 __syncwarp();
-                constexpr int WP = 32 * IT;  // points of the warp
-                const int* pre = s_pre + warp * WP;
-                const int* wrs = s_rs + warp * WP;
-                const int* wpo = s_po + warp * WP;
-                // kCopyBatch entries per lane at a time: all sources are located
-                // first, then all loads issued, then all stores (the pool reads
-                // are gathers, so latency is hidden by having many in flight).
+                int pre = wexcl;
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    if (cp[i]) {
+                        lpre[before] = pre;
+                        lsrc[before] = po[i];
+                        ldst[before] = rsv[i];
+                        atomicOr(&bm[pre >> 5], 1u << (pre & 31));
+                        ++before;
+                    }
+                    pre += c[i];
+                }
+                __syncwarp();
+                // row starts before each bitmap word
+                const int nwords = (wtot + 31) >> 5;
+                for (int w0 = 0; w0 < nwords; w0 += 32) {
+                    const int w = w0 + lane;
+                    const int cnt = w < nwords ? __popc(bm[w]) : 0;
+                    const int inc = warp_incl_scan(cnt, lane);
+                    const int carry = w0 > 0 ? wb[w0 - 1] + __popc(bm[w0 - 1]) : 0;
+                    if (w < nwords) wb[w] = carry + inc - cnt;
+                    __syncwarp();
+                }
+                // kCopyBatch bitmap words (32 entries each, one per lane) at a
+                // time: entry e's row is the last row starting at or before e;
+                // all loads are issued before the stores
                 constexpr int kCopyBatch = 8;
-                for (int e0 = 0; e0 < wtot; e0 += 32 * kCopyBatch) {
+                const unsigned le_mask = lane == 31 ? ~0u : (2u << lane) - 1u;
+                for (int w0 = 0; w0 < nwords; w0 += kCopyBatch) {
                     int src[kCopyBatch], dst[kCopyBatch];
 #pragma unroll
                     for (int u = 0; u < kCopyBatch; ++u) {
-                        const int e = e0 + u * 32 + lane;
-                        int lo = 0;  // last point of the warp with pre <= e (pre[0] = 0)
-#pragma unroll
-                        for (int step = WP / 2; step >= 1; step >>= 1)
-                            if (pre[lo + step] <= e) lo += step;
-                        const int t = e - pre[lo];
-                        src[u] = e < wtot ? wpo[lo] + t : -1;
-                        dst[u] = wrs[lo] + t;
+                        const int w = w0 + u;
+                        const int e = 32 * w + lane;
+                        src[u] = -1;
+                        dst[u] = 0;
+                        if (w < nwords && e < wtot) {
+                            const int row = wb[w] + __popc(bm[w] & le_mask) - 1;
+                            const int t = e - lpre[row];
+                            src[u] = lsrc[row] + t;
+                            dst[u] = ldst[row] + t;
+                        }
                     }
                     int cv[kCopyBatch];
                     float dv[kCopyBatch];
@@ -655,7 +700,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
                         }
                     }
                 }
-                __syncwarp();  // s_pre / s_rs / s_po are rewritten by the next sub-tile
+                __syncwarp();  // the warp's lists and bitmap are rewritten by the next sub-tile
             }
             prefix += stot;
         }
@@ -1148,10 +1193,9 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
     }
 }
 
-// Rows with |S_i| <= kFast are kept whole by the collect walk (one 32-key
-// slot per query in shared memory) and sorted there; longer rows are left to
-// the emit walk, which selects the k smallest keys on its own.
-constexpr int kFast = 24;
+// Rows with |S_i| <= kFast are kept whole by the collect walk (one slot per
+// key in shared memory) and sorted there; longer rows are left to the emit
+// walk, which selects the k smallest keys on its own.
 constexpr int kChunkGroup = 2;  // consecutive chunks a warp takes at a time
 constexpr int kRowSlots = kFast + 1;   // a row also holds the query's own key while collecting
 constexpr int kRowStride = kFast + 1;  // = kRowSlots; odd, so row starts of lanes 0..15 fall in distinct banks
