@@ -128,6 +128,18 @@ def radius_graph(x: np.ndarray, r: float, k: int, queries=None, with_d2: bool = 
     return row_ptr, col[:e]
 
 
+def knn_graph(x: np.ndarray, k: int, queries=None, with_d2: bool = False):
+    """Rows of the exact k-nearest-neighbour graph (no radius cut), CSR form:
+    row i holds the min(k, n - 1) points j != i smallest by (d2, j), in that
+    order.  This is the radius graph with an unbounded radius: every other
+    point is in S_i, and the cap keeps the k nearest.  Paper: Sec. 3.1 (exact
+    kNN search over the embedded points, Faiss IndexFlat), here without the
+    radius cut that follows it there."""
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    return radius_graph(x, float("inf"), k, queries=queries, with_d2=with_d2)
+
+
 def grid_threshold(r: float) -> int:
     """floor(r2 * 65536) for r2 = fl32(r * r), in exact rational arithmetic.
 

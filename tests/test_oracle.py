@@ -362,3 +362,56 @@ def test_components_equal_networkx(cut):
     for comp in nx.connected_components(g):
         want[list(comp)] = min(comp)
     np.testing.assert_array_equal(labels, want)
+
+
+# --------------------------------------------------------------------------
+# exact kNN (no radius cut), Sec. 3.1 without the cut
+
+def test_knn_line_closed_form():
+    # points m/256 on axis 0, m = 0..L-1: row m takes its k nearest by (d2, j);
+    # with k = 3 an interior row is [m-1, m+1, m-2] (d2 1, 1, 4 grid steps^2,
+    # the tie broken by index), the ends reach three steps along the line
+    L = 12
+    x = np.zeros((L, 2), np.float32)
+    x[:, 0] = np.arange(L) / 256.0
+    rp, col, d2 = oracle.knn_graph(x, 3, with_d2=True)
+    rows = rows_of(rp, col)
+    step2 = np.float32(1 / 256.0) ** 2
+    assert rows[0] == [1, 2, 3] and rows[L - 1] == [L - 2, L - 3, L - 4]
+    assert rows[1] == [0, 2, 3]
+    for m in range(2, L - 2):
+        assert rows[m] == [m - 1, m + 1, m - 2]
+    assert np.allclose(d2[rp[5]:rp[6]], np.array([1, 1, 4], np.float32) * step2)
+
+
+def test_knn_small_event_takes_every_point():
+    # n <= k + 1: every other point, sorted by (d2, j)
+    x = np.array([[0, 0], [3, 0], [1, 0], [1, 0]], np.float32) / 256.0
+    rp, col = oracle.knn_graph(x, 8)
+    assert rows_of(rp, col) == [[2, 3, 1], [2, 3, 0], [3, 0, 1], [2, 0, 1]]
+
+
+def test_knn_identical_points_keep_lowest_indices():
+    x = np.zeros((9, 3), np.float32)
+    rp, col = oracle.knn_graph(x, 4)
+    rows = rows_of(rp, col)
+    for i in range(9):
+        assert rows[i] == [j for j in range(9) if j != i][:4]
+
+
+@pytest.mark.parametrize("seed,n,d,k", [(0, 400, 3, 1), (1, 700, 8, 16), (2, 300, 12, 40)])
+def test_knn_distances_equal_ckdtree(seed, n, d, k):
+    # on the 1/256 grid d2 is exact in float32, so the row's d2 sequence
+    # equals cKDTree's k nearest distances squared (ties are index-free here)
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    x = (np.rint(rng.uniform(-1, 1, (n, d)) * 256) / 256).astype(np.float32)
+    rp, col, d2 = oracle.knn_graph(x, k, with_d2=True)
+    dist, idx = cKDTree(x.astype(np.float64)).query(x.astype(np.float64), k + 1)
+    for i in range(n):
+        ref = np.sort(dist[i] ** 2)[1:]  # the query itself is one of the zero distances
+        got = d2[rp[i]:rp[i + 1]].astype(np.float64)
+        assert got.size == k
+        assert np.allclose(got, ref, rtol=1e-9, atol=0)
+        assert np.all(np.diff(got) >= 0)
+        assert i not in set(col[rp[i]:rp[i + 1]].tolist())
