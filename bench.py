@@ -50,6 +50,7 @@ L2_BYTES = 126 * 1024 * 1024
 # summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
 # kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
+KNN_K = 16       # k of the exact-kNN measurement
 MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b90da92e8002", "bytes_per_point": 439_689_472 / 4_800_000}
 
 
@@ -500,6 +501,26 @@ def main(argv=None):
                     "note": "frnn_label_components: weakly connected components of the step's graphs "
                             "(all edges kept), 4 kernels, after the build on the same stream"}
 
+    # ---- exact k nearest neighbours (no radius) of the same batch
+    knn = None
+    knn_k = KNN_K
+    if n_total * knn_k <= plan.edge_capacity:
+        with torch.cuda.stream(stream):
+            plan.knn_batched(x_dev, off, knn_k, stream=stream)
+            ke0, ke1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            knn_ms = []
+            for _ in range(5):
+                ke0.record(stream)
+                plan.knn_batched(x_dev, off, knn_k, stream=stream)
+                ke1.record(stream)
+                ke1.synchronize()
+                knn_ms.append(ke0.elapsed_time(ke1))
+        if plan.last_status(stream) == 0:
+            kms = float(np.median(knn_ms))
+            knn = {"k": knn_k, "ms_per_step": kms, "events_per_s": B / (kms / 1e3),
+                   "note": "frnn_knn_graph_batched: the k nearest of every point (no radius) over the step's "
+                           "events, device time per step, median of 5 after one warm-up"}
+
     # ---- per-stage times of the batched build (CUDA events between stages)
     stage_ms = {s: [] for s in STAGES}
     with torch.cuda.stream(stream):
@@ -630,6 +651,7 @@ def main(argv=None):
                          "alu_view": alu},
             "e2e": e2e,
             "labeling": labeling,
+            "knn": knn,
             "served": served,
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_BUILD * args.steps,

@@ -236,6 +236,25 @@ FRNN_API int frnn_edge_features(frnn_plan* plan, const float* emb, int64_t e_beg
                                 void* stream);
 
 /*
+ * Exact k-nearest-neighbour graphs of a batch of events, with no radius: the
+ * paper's kNN route (Sec. 3.1, Faiss IndexFlat exact kNN) without the radius
+ * cut that follows it there.  Row i of event b holds the k_b = min(k, n_b - 1)
+ * points j != i smallest by (d2, j), d2 as in frnn_build_graph (float32,
+ * dims summed in order, no fused multiply-add), in increasing (d2, j) order;
+ * so every row of an event has the same length.  Arguments, layout and
+ * ownership as frnn_build_graph_batched (no radius; 1 <= k <= k_max_cap);
+ * the total sum_b n_b k_b must fit the plan's edge capacity (else
+ * FRNN_ERR_CAPACITY, nothing enqueued).  An event holding NaN or Inf keeps
+ * its row lengths, its entries are -1 (d2 +Inf) and FRNN_ERR_NONFINITE_INPUT
+ * is latched.  The result is the plan's last build for frnn_label_components
+ * (cut d2_max = +Inf keeps every edge; a finite cut needs FRNN_EMIT_D2) and
+ * frnn_edge_features.  Asynchronous on `stream`; not captured in a CUDA
+ * graph.  Errors: INVALID_ARG, CAPACITY, CUDA; TIMEOUT may be latched.
+ */
+FRNN_API int frnn_knn_graph_batched(frnn_plan* plan, const float* emb, const int64_t* ev_off, int n_events,
+                                   int d, int k, void* stream, frnn_csr* out);
+
+/*
  * Synchronise `stream`, then return and clear the status latched by the
  * plan's kernels since the last call (FRNN_OK if none).  If several errors
  * were latched the most severe is returned, in the order TIMEOUT, OVERFLOW,

@@ -34,7 +34,7 @@ ABI_FUNCTIONS = (
     "frnn_get_last_status", "frnn_status_string", "frnn_version", "frnn_build_graph_noalloc",
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
-    "frnn_label_components", "frnn_edge_features",
+    "frnn_label_components", "frnn_edge_features", "frnn_knn_graph_batched",
 )
 
 
@@ -85,6 +85,7 @@ def load():
     lib.frnn_plan_get_tuning.argtypes = [vp, P(frnn_tuning)]
     lib.frnn_build_graph.argtypes = [vp, vp, i64, i32, f32, i32, vp, P(frnn_csr)]
     lib.frnn_build_graph_batched.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp, P(frnn_csr)]
+    lib.frnn_knn_graph_batched.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, i32, vp, P(frnn_csr)]
     lib.frnn_build_graph_host.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp, vp, i64,
                                           vp, P(ctypes.c_int64), vp]
     lib.frnn_build_graph_profiled.argtypes = [vp, vp, P(ctypes.c_int64), i32, i32, f32, i32, vp,
@@ -302,6 +303,20 @@ class Plan:
         self._last_n = n
         return Csr(c, self.device, off, self.edge_capacity)
 
+    def knn_batched(self, emb, ev_off, k: int, stream=None) -> Csr:
+        """frnn_knn_graph_batched: exact k-nearest-neighbour rows (no radius)
+        of every event; row lengths min(k, n_b - 1)."""
+        ptr, n, d = self._emb_ptr(emb)
+        off = np.ascontiguousarray(ev_off, dtype=np.int64)
+        if off.ndim != 1 or off.size < 2 or off[-1] != n:
+            raise ValueError("ev_off must hold n_events + 1 offsets ending at emb.shape[0]")
+        c = frnn_csr()
+        _check(load().frnn_knn_graph_batched(self._h, ptr, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                             off.size - 1, d, int(k), _stream_handle(stream), ctypes.byref(c)),
+               "frnn_knn_graph_batched")
+        self._last_n = n
+        return Csr(c, self.device, off, self.edge_capacity)
+
     STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
 
     def build_profiled(self, emb, ev_off, r: float, k: int, stream=None):
@@ -344,7 +359,7 @@ class Plan:
         torch = _torch()
         n = int(self._last_n)
         labels = out if out is not None else torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
-        _check(load().frnn_label_components(self._h, float(min(d2_max, 3.0e38)), _stream_handle(stream),
+        _check(load().frnn_label_components(self._h, float(d2_max), _stream_handle(stream),
                                             labels.data_ptr()), "frnn_label_components")
         return labels[:n]
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <new>
 
 #include "frnn.h"
@@ -245,7 +246,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
         ev[b].chunk_off = chunks;
         ev[b].nchunk = nc;
         ev[b].cell_budget = (int)(cpp * nb + 4096);
-        ev[b].pad0 = ev[b].pad1 = 0;
+        ev[b].edge0 = ev[b].pad1 = 0;
         chunks += nc;
     }
     h->emb = emb;
@@ -260,6 +261,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->g_max = p->tuning.g_max;
     h->cell_scale = p->tuning.cell_scale;
     h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
+    h->knn = 0;
     h->edge_capacity = p->edge_cap;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -475,6 +477,92 @@ int frnn_build_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_o
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
     return build_batched(p, emb, ev_off, n_events, d, r, k_max, static_cast<cudaStream_t>(stream), out);
+}
+
+int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, int k,
+                           void* stream, frnn_csr* out)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    if (k < 1) return FRNN_ERR_INVALID_ARG;
+    long long n_total = 0;
+    // the argument checks of the radius build, with a radius that passes them
+    int rc = check_build_args(p, emb, ev_off, n_events, d, 1.0f, k, out, &n_total);
+    if (rc != FRNN_OK) return rc;
+    long long edges = 0;
+    for (int b = 0; b < n_events; ++b) {
+        const long long nb = ev_off[b + 1] - ev_off[b];
+        edges += nb * (long long)(nb - 1 < k ? (nb > 0 ? nb - 1 : 0) : k);
+    }
+    if (edges > p->edge_cap) return FRNN_ERR_CAPACITY;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevState& st = p->st;
+    out->row_ptr = st.row_ptr;
+    out->col = st.col;
+    out->d2 = (p->prm.flags & FRNN_EMIT_D2) ? st.d2 : nullptr;
+    out->edge_off = st.edge_off;
+    out->n_edges = st.edge_off + n_events;
+    out->n_events = n_events;
+    out->n_total = n_total;
+    const float inf = std::numeric_limits<float>::infinity();
+    if (n_total == 0) {
+        if (cudaMemsetAsync(st.row_ptr, 0, sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(st.edge_off, 0, sizeof(int) * (n_events + 1), s) != cudaSuccess)
+            return FRNN_ERR_CUDA;
+        p->last = *out;
+        p->last_r2 = inf;
+        p->has_last = true;
+        return FRNN_OK;
+    }
+    const int slot = p->ring_pos;
+    p->ring_pos = (p->ring_pos + 1) % kRing;
+    if (cudaEventSynchronize(p->ring_ev[slot]) != cudaSuccess) return FRNN_ERR_CUDA;
+    CallHdr* h = reinterpret_cast<CallHdr*>(p->h_call[slot]);
+    EvDesc* ev = reinterpret_cast<EvDesc*>(p->h_call[slot] + sizeof(CallHdr));
+    const int cpp = p->prm.cells_per_point;
+    int chunks = 0;
+    long long e0 = 0;
+    for (int b = 0; b < n_events; ++b) {
+        const long long nb = ev_off[b + 1] - ev_off[b];
+        const int nc = nb > 0 ? (int)((nb + kChunk - 1) / kChunk) : 1;
+        ev[b].pt_off = ev_off[b];
+        ev[b].n = (int)nb;
+        ev[b].chunk_off = chunks;
+        ev[b].nchunk = nc;
+        ev[b].cell_budget = (int)(cpp * nb + 4096);
+        ev[b].edge0 = (int)e0;
+        ev[b].pad1 = 0;
+        chunks += nc;
+        e0 += nb * (long long)(nb - 1 < k ? (nb > 0 ? nb - 1 : 0) : k);
+    }
+    h->emb = emb;
+    h->n_total = n_total;
+    h->n_events = n_events;
+    h->total_chunks = chunks;
+    h->d = d;
+    h->dp = (d + 3) & ~3;
+    h->k = k;
+    h->r = 0.f;
+    h->r2 = inf;
+    h->g_max = p->tuning.g_max;
+    h->cell_scale = p->tuning.cell_scale;
+    h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
+    h->knn = 1;
+    h->edge_capacity = p->edge_cap;
+    const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
+    if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FRNN_ERR_CUDA;
+    if (cudaEventRecord(p->ring_ev[slot], s) != cudaSuccess) return FRNN_ERR_CUDA;
+    const int cap = next_pow2((k > 32 ? k : 32) + 32);
+    LaunchCfg cfg;
+    rc = get_walk_cfg(p, h->dp / 4, cap, &cfg);
+    if (rc != FRNN_OK) return rc;
+    if (launch_knn(st, h->dp / 4, cfg, s) != 0) return FRNN_ERR_CUDA;
+    p->last = *out;
+    p->last_r2 = inf;
+    p->has_last = true;
+    return FRNN_OK;
 }
 
 int frnn_build_graph_profiled(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,

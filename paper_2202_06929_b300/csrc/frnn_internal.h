@@ -38,6 +38,7 @@ struct CallHdr {
     int g_max;           // tuning: most hashed dims
     float cell_scale;    // tuning: cell edge / r (>= 1)
     int emit_d2;
+    int knn;             // 1: k nearest with no radius (cell edge from density; r unused)
     long long edge_capacity;
 };
 
@@ -47,7 +48,8 @@ struct EvDesc {
     int chunk_off;       // first chunk of the event
     int nchunk;          // chunks (>= 1, also for an empty event)
     int cell_budget;     // cell slots the event may use
-    int pad0, pad1;
+    int edge0;           // kNN builds: first edge of the event (rows of fixed length)
+    int pad1;
 };
 
 // Written on the device by the planning step (one per event).
@@ -125,5 +127,7 @@ int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int
 int launch_edge_features(const DevState& st, const float* emb, long long e_begin, long long e_end, float* out,
                          int grid, void* stream);
 int config_pt(int n_sm, LaunchCfg* cfg);
+// The k-nearest-neighbour build (no radius): grid, fixed-length rows, ring walk.
+int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream);
 
 }  // namespace frnn

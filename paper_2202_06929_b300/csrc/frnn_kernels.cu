@@ -159,9 +159,11 @@ __device__ void plan_event(const DevState& st, const CallHdr& h, int b, const Ev
         pl.inv_s = 1.0f / h.r;
         pl.skip = __ldcg(&st.nonfinite[b]) ? 1 : 0;
         if (!pl.skip && e.n > 0) {
-            // widest dims first (ties: lower index)
+            // widest dims first (ties: lower index); radius builds grid at
+            // most g_max of them, kNN builds up to kMaxG
             int picks[kMaxG];
-            const int npick = min(min(h.g_max, kMaxG), D);
+            const int npick_all = min(kMaxG, D);
+            const int npick = h.knn ? npick_all : min(min(h.g_max, kMaxG), D);
             unsigned long long used = 0ull;
             for (int i = 0; i < npick; ++i) {
                 int best = -1;
@@ -173,24 +175,57 @@ __device__ void plan_event(const DevState& st, const CallHdr& h, int b, const Ev
                 picks[i] = best;
                 used |= 1ull << best;
             }
-            float s = h.r * h.cell_scale * kCellMargin;
             const int maxc0 = min(e.cell_budget, kMaxDimCells);
             const float w0 = s_w[picks[0]];
-            if (w0 / s > (float)(maxc0 - 3)) s = (w0 / (float)(maxc0 - 3)) * kCellMargin;
-            int g = 0;
-            long long cells = 1;
-            for (int i = 0; i < npick; ++i) {
-                const int t = picks[i];
-                const float a = s_w[t] / s;
-                const int nc = (a >= (float)(kMaxDimCells - 1)) ? kMaxDimCells : (int)a + 1;
-                if (g > 0 && nc < 4) break;
-                if (g > 0 && cells * nc > (long long)e.cell_budget) break;
-                pl.dims[g] = t;
-                pl.ncell[g] = nc;
-                pl.lo[g] = s_lo[t];
-                cells *= nc;
-                ++g;
+            // Grid of cell edge s over the picked dims, widest first: a dim is
+            // added while it has >= 4 cells and the table fits the budget.
+            auto grid_dims = [&](float s, int gmax, long long* cells_out) {
+                int g = 0;
+                long long cells = 1;
+                for (int i = 0; i < gmax; ++i) {
+                    const int t = picks[i];
+                    const float a = s_w[t] / s;
+                    const int nc = (a >= (float)(kMaxDimCells - 1)) ? kMaxDimCells : (int)a + 1;
+                    if (g > 0 && nc < 4) break;
+                    if (g > 0 && cells * nc > (long long)e.cell_budget) break;
+                    pl.dims[g] = t;
+                    pl.ncell[g] = nc;
+                    pl.lo[g] = s_lo[t];
+                    cells *= nc;
+                    ++g;
+                }
+                *cells_out = cells;
+                return g;
+            };
+            float s;
+            int gsel = npick;
+            if (!h.knn) {
+                // radius graph: cell edge >= r (with the float32 binning margin)
+                s = h.r * h.cell_scale * kCellMargin;
+            } else {
+                // k nearest: cell edge = the distance to the k-th neighbour
+                // at the event's mean density in all D' dims of nonzero
+                // extent (k points in a D'-ball of that radius), so that the
+                // 3^g cells around a point usually hold its k nearest (speed
+                // only: the ring walk widens until they are certain)
+                int dpos = 0;
+                float logv = 0.f;
+                for (int t = 0; t < D; ++t)
+                    if (s_w[t] > 0.f) {
+                        logv += logf(s_w[t]);
+                        ++dpos;
+                    }
+                s = 1.f;
+                if (dpos > 0) {
+                    const float hd = 0.5f * (float)dpos;
+                    const float logball = hd * logf(3.14159265f) - lgammaf(hd + 1.f);
+                    const float rk = expf((logf((float)max(h.k, 1)) + logv - logf((float)e.n) - logball) / (float)dpos);
+                    if (rk > 0.f && isfinite(rk)) s = rk * h.cell_scale;
+                }
             }
+            if (w0 / s > (float)(maxc0 - 3)) s = (w0 / (float)(maxc0 - 3)) * kCellMargin;
+            long long cells;
+            const int g = grid_dims(s, gsel, &cells);
             pl.g = g;
             pl.stride[g - 1] = 1;
             for (int t = g - 2; t >= 0; --t) pl.stride[t] = pl.stride[t + 1] * pl.ncell[t + 1];
@@ -1107,6 +1142,76 @@ __device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int2* run
     if (cnt > 0) body(make_runs(gbeg, glen, lane));
 }
 
+// Calls body(Runs) for the cells of ring rho >= 2 around the segment's cell
+// (Chebyshev distance exactly rho along the gridded dims; ring 1 is the 3^g
+// block of for_each_run_group).  Each combination of offsets in [-rho, rho]
+// along the g-1 slower dims gives two slots: if the combination reaches rho,
+// slot 0 is the whole run of cells k-rho .. k+rho along the fastest dim and
+// slot 1 is empty; otherwise the slots are the two end cells k-rho and k+rho.
+// Non-empty slots are packed into groups of at most 32 runs.
+template <typename Body>
+__device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const int* cell_start, int lane,
+                                                    Body&& body)
+{
+    const EvPlan& pl = ww.pl;
+    const int g = pl.g;
+    const int side = 2 * rho + 1;
+    int ncomb = 1;
+    for (int t = 0; t < g - 1; ++t) ncomb *= side;
+    const int nslot = 2 * ncomb;
+    const int kl = ww.ks[g - 1], ncl = pl.ncell[g - 1];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int cnt = 0, gbeg = 0, glen = 0;
+    for (int r0 = 0; r0 < nslot; r0 += 32) {
+        const int si = r0 + lane;
+        int beg = 0, len = 0;
+        if (si < nslot) {
+            int rem = si >> 1, cb = 0, reach = 0;
+            bool ok = true;
+            for (int t = 0; t < g - 1; ++t) {
+                const int o = rem % side - rho;
+                rem /= side;
+                const int kt = ww.ks[t] + o;
+                ok &= (kt >= 0) && (kt < pl.ncell[t]);
+                cb += kt * pl.stride[t];
+                reach = max(reach, abs(o));
+            }
+            int c0 = 0, c1 = -1;  // fastest-dim cells of this slot
+            if (reach == rho) {
+                if ((si & 1) == 0) {
+                    c0 = max(kl - rho, 0);
+                    c1 = min(kl + rho, ncl - 1);
+                }
+            } else {
+                const int c = (si & 1) ? kl + rho : kl - rho;
+                if (c >= 0 && c < ncl) c0 = c1 = c;
+            }
+            if (ok && c1 >= c0) {
+                beg = cell_start[pl.cell_off + cb + c0];
+                len = cell_start[pl.cell_off + cb + c1 + 1] - beg;
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, len > 0);
+        const int nne = __popc(m);
+        if (cnt + nne > 32) {
+            body(make_runs(gbeg, glen, lane));
+            cnt = 0;
+            gbeg = 0;
+            glen = 0;
+        }
+        if (len > 0) ww.stage[cnt + __popc(m & lt_mask)] = make_int2(beg, len);
+        __syncwarp();
+        if (lane >= cnt && lane < cnt + nne) {
+            const int2 v = ww.stage[lane];
+            gbeg = v.x;
+            glen = v.y;
+        }
+        __syncwarp();
+        cnt += nne;
+    }
+    if (cnt > 0) body(make_runs(gbeg, glen, lane));
+}
+
 // Sorted position of candidate number qi of the segment (or -1 past the end).
 __device__ __forceinline__ int candidate_at(const Runs& rn, int qi)
 {
@@ -1543,6 +1648,212 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(De
     }
 }
 
+// ---------------------------------------------------------------------------
+// k nearest neighbours with no radius (Sec. 3.1's exact kNN, without the cut).
+constexpr int kKnnMaxRing = 32;        // rings walked before the whole-event scan
+constexpr long long kKnnMaxComb = 4096;  // slower-dim offset combinations of one ring, at most
+// Rows have the fixed length k_b = min(k, n_b - 1), so their offsets need no
+// count: row p of event b starts at edge0_b + (p - pt_off_b) k_b.
+__global__ void __launch_bounds__(kPtThreads) k_knn_rows(DevState st)
+{
+    const long long P = st.hdr->n_total;
+    const int B = st.hdr->n_events;
+    const int K = st.hdr->k;
+    long long lo = 1, hi = 0, off = 0;
+    int e0 = 0, kb = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        if (p < lo || p >= hi) {
+            const int b = event_of_point(st.ev, B, p);
+            off = st.ev[b].pt_off;
+            lo = off;
+            hi = off + st.ev[b].n;
+            e0 = st.ev[b].edge0;
+            kb = min(K, st.ev[b].n - 1);
+        }
+        st.row_ptr[p] = e0 + (int)(p - off) * kb;
+        st.cnt_o[p] = kb;  // the labeling pass reads row lengths from here
+    }
+    if (blockIdx.x == 0) {
+        for (int b = threadIdx.x; b <= B; b += blockDim.x) {
+            int e;
+            if (b < B) {
+                e = st.ev[b].edge0;
+            } else {
+                const EvDesc last = st.ev[B - 1];
+                e = last.edge0 + last.n * max(min(K, last.n - 1), 0);
+            }
+            st.edge_off[b] = e;
+            if (b == B) st.row_ptr[P] = e;
+        }
+    }
+}
+
+// The kNN walk.  A warp takes two consecutive points in cell order (walked
+// together when they share a cell, as in the emit walk) and visits the 3^g
+// block of cells around them, then rings of cells at Chebyshev distance
+// rho = 2, 3, ... along the gridded dims.  After ring rho every point not yet
+// visited lies at least rho - 1/64 cell edges away along some gridded dim
+// (the float32 cell coordinate is within 0.006 cells of (x - lo) / s), so a
+// query is done once it holds k_b keys and its k_b-th d2 is below
+// ((rho - 1/64) s)^2 (1 - 2^-10); when the rings cover the whole grid, every
+// point has been seen.
+template <int DP4>
+__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_knn(DevState st, int cap)
+{
+    extern __shared__ float4 s_dyn[];
+    constexpr int DP = 4 * DP4;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float* sq = reinterpret_cast<float*>(s_dyn) + wib * (2 * DP);
+    const ulonglong2* sqp = reinterpret_cast<const ulonglong2*>(sq);
+    unsigned long long* keys0 = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<float*>(s_dyn) + (kFillThreads / 32) * (2 * DP)) + (size_t)wib * 2 * cap;
+    unsigned long long* keys1 = keys0 + cap;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long P = st.hdr->n_total;
+    const int K = st.hdr->k;
+    const int B = st.hdr->n_events;
+    const int emit = st.hdr->emit_d2;
+    const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
+    __shared__ WarpWalk s_ww[kFillThreads / 32];
+    WarpWalk& ww = s_ww[wib];
+    int plan_b = -1;
+    for (;;) {
+        long long qa = 0;
+        if (lane == 0) qa = (long long)atomicAdd(&st.counters[kCtrEmitRows], 2u);
+        qa = __shfl_sync(kFull, qa, 0);
+        if (qa >= P) break;
+        const long long qb = qa + 1 < P ? qa + 1 : -1;
+        const int ba = event_of_point(st.ev, B, qa);
+        const bool together = qb >= 0 && __ldg(st.cell_s + qa) == __ldg(st.cell_s + qb) &&
+                              event_of_point(st.ev, B, qb) == ba;
+        for (int pass = 0; pass < (together || qb < 0 ? 1 : 2); ++pass) {
+            const long long q0 = pass == 0 ? qa : qb;
+            const long long q1 = together ? qb : -1;
+            const int b = pass == 0 ? ba : event_of_point(st.ev, B, q0);
+            const EvDesc ev = st.ev[b];
+            const int kb = min(K, ev.n - 1);
+            if (kb <= 0) continue;
+            if (plan_b != b) {
+                load_plan(ww, st.plan, b, lane);
+                plan_b = b;
+            }
+            const int rs0 = st.row_ptr[ev.pt_off + __ldg(st.perm + q0)];
+            const int rs1 = q1 >= 0 ? st.row_ptr[ev.pt_off + __ldg(st.perm + q1)] : 0;
+            if (ww.pl.skip) {
+                // non-finite input: the event's rows keep their length and
+                // hold column -1 (d2 +inf); FRNN_ERR_NONFINITE_INPUT is latched
+                for (int e2 = lane; e2 < kb; e2 += 32) {
+                    st.col[rs0 + e2] = -1;
+                    if (emit) st.d2[rs0 + e2] = __int_as_float(0x7f800000);
+                    if (q1 >= 0) {
+                        st.col[rs1 + e2] = -1;
+                        if (emit) st.d2[rs1 + e2] = __int_as_float(0x7f800000);
+                    }
+                }
+                continue;
+            }
+            __syncwarp();
+            if (lane < DP4) {
+                const float4 v = __ldg(xs4 + q0 * DP4 + lane);
+                const float4 u = q1 >= 0 ? __ldg(xs4 + q1 * DP4 + lane) : v;
+                sq[2 * (4 * lane + 0)] = v.x; sq[2 * (4 * lane + 0) + 1] = u.x;
+                sq[2 * (4 * lane + 1)] = v.y; sq[2 * (4 * lane + 1) + 1] = u.y;
+                sq[2 * (4 * lane + 2)] = v.z; sq[2 * (4 * lane + 2) + 1] = u.z;
+                sq[2 * (4 * lane + 3)] = v.w; sq[2 * (4 * lane + 3) + 1] = u.w;
+            }
+            __syncwarp();
+            segment_cell(ww, sq, 0, lane);
+            // rings needed to cover the grid from this cell
+            int rho_max = 1;
+            for (int t = 0; t < ww.pl.g; ++t)
+                rho_max = max(rho_max, max(ww.ks[t], ww.pl.ncell[t] - 1 - ww.ks[t]));
+            const float cs = ww.pl.s;
+            unsigned long long thr0 = ~0ull, thr1 = ~0ull;
+            int nk0 = 0, nk1 = 0;
+            bool done0 = false, done1 = q1 < 0;
+            auto batch = [&](const Runs& rn) {
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    CandPk<DP4> cp;
+                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                    const float2 d = dist2_pair<DP4>(sqp, cp);
+                    const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                    const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
+                    bool t0 = !done0 && cand >= 0 && (long long)cand != q0 && k0 < thr0;
+                    bool t1 = !done1 && cand >= 0 && (long long)cand != q1 && k1 < thr1;
+                    unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
+                    if (nk0 + 32 > cap && m0) {
+                        warp_sort_smem(keys0, nk0, lane);
+                        nk0 = kb;
+                        thr0 = keys0[kb - 1];
+                        t0 = t0 && k0 < thr0;
+                        m0 = __ballot_sync(kFull, t0);
+                    }
+                    if (nk1 + 32 > cap && m1) {
+                        warp_sort_smem(keys1, nk1, lane);
+                        nk1 = kb;
+                        thr1 = keys1[kb - 1];
+                        t1 = t1 && k1 < thr1;
+                        m1 = __ballot_sync(kFull, t1);
+                    }
+                    if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
+                    if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
+                    nk0 += __popc(m0);
+                    nk1 += __popc(m1);
+                    __syncwarp();
+                }
+            };
+            const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
+            for (int rho = 1;; ++rho) {
+                // past kKnnMaxRing rings, or kKnnMaxComb offset combinations
+                // in one ring (a far outlier stretching the grid), the walk
+                // starts over and scans the whole event once as a single run
+                long long ncomb = 1;
+                for (int t = 0; t < ww.pl.g - 1 && ncomb <= kKnnMaxComb; ++t) ncomb *= 2 * rho + 1;
+                if (rho > 1 && (rho > kKnnMaxRing || ncomb > kKnnMaxComb)) {
+                    nk0 = nk1 = 0;
+                    thr0 = thr1 = ~0ull;
+                    done0 = false;
+                    done1 = q1 < 0;
+                    const int ev_beg = st.cell_start[ww.pl.cell_off];
+                    const int ev_len = st.cell_start[ww.pl.cell_off + ww.pl.n_cells] - ev_beg;
+                    batch(make_runs(lane == 0 ? ev_beg : 0, lane == 0 ? ev_len : 0, lane));
+                    if (!done0) {
+                        warp_sort_smem(keys0, nk0, lane);
+                        nk0 = min(nk0, kb);
+                    }
+                    if (!done1) {
+                        warp_sort_smem(keys1, nk1, lane);
+                        nk1 = min(nk1, kb);
+                    }
+                    break;
+                }
+                if (rho == 1) for_each_run_group(ww, run_tab, st.cell_start, lane, batch);
+                else for_each_ring_group(ww, rho, st.cell_start, lane, batch);
+                // keep the k_b smallest keys of each row and test its stop rule
+                const float lim = (float)rho - 1.0f / 64.0f;
+                const float cov = (lim * cs) * (lim * cs) * (1.0f - 1.0f / 1024.0f);
+                if (!done0 && nk0 >= kb) {
+                    warp_sort_smem(keys0, nk0, lane);
+                    nk0 = kb;
+                    thr0 = keys0[kb - 1];
+                    done0 = __uint_as_float((unsigned)(thr0 >> 32)) < cov;
+                }
+                if (!done1 && nk1 >= kb) {
+                    warp_sort_smem(keys1, nk1, lane);
+                    nk1 = kb;
+                    thr1 = keys1[kb - 1];
+                    done1 = __uint_as_float((unsigned)(thr1 >> 32)) < cov;
+                }
+                if ((done0 && done1) || rho >= rho_max) break;
+            }
+            emit_row_out(st, keys0, nk0, rs0, kb, emit, lane);
+            if (q1 >= 0) emit_row_out(st, keys1, nk1, rs1, kb, emit, lane);
+        }
+    }
+}
+
 // Stage boundaries: ev[i] is recorded before stage i and ev[7] after the last
 // (all NULL for an untimed build).
 inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
@@ -1587,6 +1898,8 @@ cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_walk_emit<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_walk_knn<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
+    if (e != cudaSuccess) return e;
     int nb_c = 0, nb_f = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4>, kWalkThreads, csm);
     if (e != cudaSuccess) return e;
@@ -1600,6 +1913,14 @@ cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
 }
 
 }  // namespace
+
+template <int DP4>
+cudaError_t launch_knn_walk(const DevState& st, const LaunchCfg& cfg, cudaStream_t s)
+{
+    k_knn_rows<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_walk_knn<DP4><<<cfg.grid_fill, kFillThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
+    return cudaGetLastError();
+}
 
 #define FRNN_DP4_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
@@ -1619,6 +1940,23 @@ int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream
     if (e != cudaSuccess) return (int)e;
     switch (dp4) {
 #define FRNN_CASE(n) case n: return (int)launch_walks<n>(st, cfg, s, ev);
+        FRNN_DP4_CASES(FRNN_CASE)
+#undef FRNN_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_bbox_plan<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_key_hist<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
+    k_scatter<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    switch (dp4) {
+#define FRNN_CASE(n) case n: return (int)launch_knn_walk<n>(st, cfg, s);
         FRNN_DP4_CASES(FRNN_CASE)
 #undef FRNN_CASE
         default: return (int)cudaErrorInvalidValue;

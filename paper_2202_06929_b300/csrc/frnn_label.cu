@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* 
         if ((long long)re <= ecap) {
             for (int e = rs; e < re; ++e) {
                 if (use_d2 && !(st.d2[e] <= d2_max)) continue;
-                m = min(m, off + st.col[e]);
+                const int c = st.col[e];
+                if (c >= 0) m = min(m, off + c);  // -1: entry of an event with non-finite input
             }
         }
         parent[p] = (int)m;
@@ -150,7 +151,9 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int*
         int rp = -1;
         for (int e = rs; e < re; ++e) {
             if (use_d2 && !(st.d2[e] <= d2_max)) continue;
-            const long long q = off + st.col[e];
+            const int c = st.col[e];
+            if (c < 0) continue;  // entry of an event with non-finite input (kNN builds)
+            const long long q = off + c;
             if (q < p && (!any_capped || st.cnt_o[q] < K)) continue;
             if (rp < 0) rp = __ldcg(parent + p);  // an ancestor of p (its root after compression)
             const int pq = __ldcg(parent + q);
@@ -241,9 +244,12 @@ __global__ void __launch_bounds__(kLabelThreads) k_edge_features(DevState st, co
         for (long long t = lane; t < nel; t += 32) {
             const long long e = a + t / W;
             const int f = (int)(t % W);
-            const float* xj = emb + (off + st.col[e]) * D;
+            const int c = st.col[e];
+            const float* xj = emb + (off + (c >= 0 ? c : 0)) * D;
             float v;
-            if (f < D) {
+            if (c < 0) {
+                v = __int_as_float(0x7fc00000);  // entry of an event with non-finite input: NaN features
+            } else if (f < D) {
                 v = xi[f];
             } else if (f < 2 * D) {
                 v = xj[f - D];
