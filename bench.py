@@ -69,6 +69,8 @@ def parse_args(argv=None):
                     help="queries of the CPU oracle sample (bounded CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-slots", type=int, default=3, help="server slots of the end-to-end measurement")
+    ap.add_argument("--e2e-batch", type=int, default=0, help="events per server batch (default: a quarter of a step)")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-requests", type=int, default=2000,
                     help="measured requests per offered load (plus 200 warm-up)")
@@ -230,6 +232,39 @@ def stage_bytes(n_total: int, n_edges: int, d: int):
         # workload): not counted
         "walk_emit": 0,
     }
+
+
+def measure_link(torch, dev, h2d_bytes: int, d2h_bytes: int, reps: int = 5):
+    """Pinned host <-> device copy bandwidth for a step's bytes: each
+    direction alone and both at once on two streams (the bound of the end to
+    end path, whose copies in and out overlap across server slots)."""
+    hi = torch.empty(h2d_bytes // 4, dtype=torch.int32).pin_memory()
+    ho = torch.empty(d2h_bytes // 4, dtype=torch.int32).pin_memory()
+    di = torch.empty(h2d_bytes // 4, dtype=torch.int32, device=dev)
+    do = torch.empty(d2h_bytes // 4, dtype=torch.int32, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / reps
+
+    def both():
+        with torch.cuda.stream(s1):
+            di.copy_(hi, non_blocking=True)
+        with torch.cuda.stream(s2):
+            ho.copy_(do, non_blocking=True)
+
+    t_in = timed(lambda: di.copy_(hi, non_blocking=True))
+    t_out = timed(lambda: ho.copy_(do, non_blocking=True))
+    t_both = timed(both)
+    return {"h2d_gbs": h2d_bytes / t_in / 1e9, "d2h_gbs": d2h_bytes / t_out / 1e9,
+            "both_gbs": (h2d_bytes + d2h_bytes) / t_both / 1e9,
+            "note": "pinned copies of one step's input and result sizes, each direction alone and both at once"}
 
 
 def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point: int, sample: int = 100_000,
@@ -545,9 +580,9 @@ def main(argv=None):
         xin = pinned_x.numpy()
         e2e_steps = max(3, min(args.steps, 10))
         sizes = np.diff(off)
-        per_batch = max(1, B // 4)
+        per_batch = args.e2e_batch or max(1, B // 4)
         srv = frnn.Server(d=d, r=r, k=k, batch_points=int(per_batch * n_max_event), batch_events=per_batch,
-                          slots=3, edges_per_point=epp, device=local)
+                          slots=args.e2e_slots, edges_per_point=epp, device=local)
         try:
             req_start = np.tile(off[:-1], e2e_steps)
             req_len = np.tile(sizes, e2e_steps)
@@ -559,11 +594,14 @@ def main(argv=None):
             srv.close()
         e2e_s = max_over_ranks(pg, res["wall_s"], dev)
         d2h = int(4 * (n_total + B) + 4 * n_edges)
+        link = measure_link(torch, dev, int(x_host.nbytes), d2h)
         e2e = {"value": sum_over_ranks(pg, float(B * e2e_steps), dev) / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(x_host.nbytes), "d2h_bytes_per_step": d2h,
                "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+               "link": link,
+               "frac_of_link": ((x_host.nbytes + d2h) * e2e_steps / e2e_s / 1e9) / link["both_gbs"],
                "note": (f"frnn_server_run_trace: {B * e2e_steps} events present at t=0, {per_batch} events per "
-                        "batch on 3 slots; each batch: H2D of its points from pinned host memory, build, D2H "
+                        f"batch on {args.e2e_slots} slots; each batch: H2D of its points from pinned host memory, build, D2H "
                         "of row_ptr, edge_off and col into pinned host memory; host wall clock")}
         out = dict(row_ptr=torch.zeros(n_total + 1, dtype=torch.int32).pin_memory().numpy(),
                    col=torch.zeros(n_total * epp, dtype=torch.int32).pin_memory().numpy(),
