@@ -1450,18 +1450,21 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect
             }
         }
         __syncwarp();
-        // ... then the rows, cut at k, go to the pool one after another
-        unsigned fm = __ballot_sync(kFull, my_off >= 0);
-        while (fm) {
-            const int i = __ffs(fm) - 1;
-            fm &= fm - 1;
-            const int off = __shfl_sync(kFull, my_off, i);
-            const int cnti = __shfl_sync(kFull, cnt, i);
-            const unsigned long long* row = keys + i * kRowStride;
-            if (lane < cnti) {
-                const unsigned long long kk = row[lane];
-                st.pool[off + lane] = (int)(unsigned)kk;
-                if (emit) st.pool_d2[off + lane] = __uint_as_float((unsigned)(kk >> 32));
+        // ... then the rows, cut at k, go to the pool: they fill
+        // [base_off, base_off + tot) in lane order, so the warp writes that
+        // range flat, each entry finding its row by binary lifting over the
+        // lanes' prefix sums
+        if (fits) {
+            const int excl = incl - need;
+            for (int e0 = 0; e0 < tot; e0 += 32) {
+                const int e = e0 + lane;
+                const int L = find_run(incl, e);
+                const int exl = __shfl_sync(kFull, excl, L);
+                if (e < tot) {
+                    const unsigned long long kk = keys[L * kRowStride + (e - exl)];
+                    st.pool[base_off + e] = (int)(unsigned)kk;
+                    if (emit) st.pool_d2[base_off + e] = __uint_as_float((unsigned)(kk >> 32));
+                }
             }
         }
         __syncwarp();
