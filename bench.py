@@ -51,7 +51,7 @@ L2_BYTES = 126 * 1024 * 1024
 # kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b90da92e8002", "bytes_per_point": 439_689_472 / 4_800_000}
+MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b741f40af440", "bytes_per_point": 435_600_384 / 4_800_000}
 
 
 def parse_args(argv=None):
