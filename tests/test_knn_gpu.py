@@ -161,3 +161,45 @@ def test_knn_far_outlier_takes_the_whole_event_scan():
     host, st = knn_gpu(x, 8)
     assert st == 0
     assert_rows_equal(host, x, 8)
+
+
+def test_knn_and_radius_builds_alternate_on_one_plan():
+    # the two launch sequences share the plan's counters and tile states:
+    # each must leave them as the other expects (radius builds replayed from
+    # a captured graph)
+    x = synth.clustered_grid(3000, 8, 14, 150, 0.03)
+    xt = torch.from_numpy(x).cuda()
+    off = np.array([0, x.shape[0]], np.int64)
+    rp_r, col_r = oracle.radius_graph(x, 0.1, 16)
+    rp_k, col_k = oracle.knn_graph(x, 12)
+    plan = frnn.Plan(n_max=x.shape[0], d_max=8, k_max_cap=16, edge_capacity=x.shape[0] * 16, use_graph=True)
+    try:
+        for _ in range(2):
+            h = plan.build_batched(xt, off, 0.1, 16).to_host()
+            assert plan.last_status() == 0
+            np.testing.assert_array_equal(h["row_ptr"], rp_r)
+            np.testing.assert_array_equal(h["col"], col_r)
+            h = plan.knn_batched(xt, off, 12).to_host()
+            assert plan.last_status() == 0
+            np.testing.assert_array_equal(h["row_ptr"], rp_k)
+            np.testing.assert_array_equal(h["col"], col_k)
+    finally:
+        plan.close()
+
+
+def test_knn_edge_features_equal_oracle():
+    x = synth.uniform_grid(1500, 6, 15)
+    k = 5
+    plan = frnn.Plan(n_max=x.shape[0], d_max=6, k_max_cap=k, edge_capacity=x.shape[0] * k)
+    try:
+        xt = torch.from_numpy(x).cuda()
+        plan.knn_batched(xt, np.array([0, x.shape[0]]), k)
+        feats = plan.edge_features(xt, 0, x.shape[0] * k).cpu().numpy()
+        assert plan.last_status() == 0
+    finally:
+        plan.close()
+    rp, col, d2 = oracle.knn_graph(x, k, with_d2=True)
+    src = np.repeat(np.arange(x.shape[0]), np.diff(rp))
+    np.testing.assert_array_equal(feats[:, :6], x[src])
+    np.testing.assert_array_equal(feats[:, 6:12], x[col])
+    np.testing.assert_array_equal(feats[:, 12], d2)
