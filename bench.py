@@ -51,7 +51,7 @@ L2_BYTES = 126 * 1024 * 1024
 # kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "b741f40af440", "bytes_per_point": 435_600_384 / 4_800_000}
+MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "df2858e41ee7", "bytes_per_point": 435_600_384 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -201,12 +201,20 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def measured_traffic(stage: str, n_total: int):
-    """roofline.traffic of the given stage, or None once the kernel source changed."""
+def kernel_source_sha1() -> str:
+    """sha1 of the kernel source with // comments removed and whitespace runs
+    collapsed: a capture stays valid across comment edits, not code edits."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2202_06929_b300", "csrc", "frnn_kernels.cu")
+    import re
+    src = open(os.path.join(ROOT, "paper_2202_06929_b300", "csrc", "frnn_kernels.cu")).read()
+    src = re.sub(r"\s+", " ", re.sub(r"//[^\n]*", "", src)).strip()
+    return hashlib.sha1(src.encode()).hexdigest()
+
+
+def measured_traffic(stage: str, n_total: int):
+    """roofline.traffic of the given stage, or None once the kernel code changed."""
     try:
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha1()
     except OSError:
         return None
     if stage != MEASURED_TRAFFIC["stage"] or not sha.startswith(MEASURED_TRAFFIC["source_sha1_prefix"]):

@@ -7,26 +7,32 @@
 // batch of one):
 //
 //   1 k_bbox_plan   per-event bounding box; the last chunk of an event picks
-//                   its cell grid (hashed dims, cell edge, strides); the last
-//                   event planned lays the events' cell tables end to end
+//                   its cell grid (gridded dims, cell edge, strides, run
+//                   table); the last event planned lays the events' cell
+//                   tables end to end
 //   2 k_key_hist    cell id of every point, histogram by atomics (the old
 //                   count is the point's slot inside its cell)
-//   3 k_scan<0>     exclusive scan of the cell histogram (decoupled look-back),
-//                   which also clears the histogram for the next build
+//   3 k_scan<0>     exclusive scan of the cell histogram (decoupled look-back
+//                   per block tile), which also clears the histogram
 //   4 k_scatter     points copied into cell order, rows padded to a multiple
 //                   of four floats for 16-byte loads
-//   5 k_walk_collect  a warp takes 32 queries in cell order; per cell it walks
-//                   the 3^(g-1) runs of neighbouring cells and counts the points
-//                   within r (|S_i|); rows of at most 32 neighbours are sorted
-//                   by (d2, j), cut at k and parked in a pool
+//   5 k_walk_collect  warps take chunks of 32 queries in cell order from a
+//                   counter; per cell they walk the 3^(g-1) runs of
+//                   neighbouring cells and count the points within r
+//                   (|S_i|); rows of at most kFast neighbours are sorted by
+//                   (d2, j), cut at k and parked in a pool
 //   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr; each parked
 //                   row is copied to its place as soon as its offset is known
-//   7 k_walk_emit   the long rows, walked again one per warp, keeping the k
-//                   smallest (d2, j) keys
+//   7 k_walk_emit   the longer rows, walked again two of a cell per warp,
+//                   keeping the k smallest (d2, j) keys
+//
+// The k-nearest-neighbour build (no radius) reuses stages 1-4 with a
+// density-sized grid, then writes fixed-length row offsets (k_knn_rows) and
+// fills the rows with a ring walk (k_walk_knn).
 //
 // Paper: Sec. 3.4 (fixed-radius neighbours by a grid of cells, cost growing
-// as 3^g with the gridded dimensions g, which is why at most four are used)
-// and Sec. 3.1 (the k nearest within the radius).
+// as 3^g with the gridded dimensions g) and Sec. 3.1 (the k nearest, within
+// the radius or, for the kNN build, without one).
 #include <cuda_runtime.h>
 
 #include <cstdint>
