@@ -50,8 +50,11 @@ L2_BYTES = 126 * 1024 * 1024
 # summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
 # kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
+# warp instructions per query of the collect walk in the same ncu capture as
+# MEASURED_TRAFFIC (1.302 G instructions for 4.8 M queries)
+MEASURED_INSTR_PER_QUERY = 1_302_432_867 / 4_800_000
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"stage": "walk_collect", "source_sha1_prefix": "df2858e41ee7", "bytes_per_point": 435_600_384 / 4_800_000}
+MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "df2858e41ee7", "bytes_per_point": 435_600_384 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -134,23 +137,32 @@ def percentile(v, q):
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 100 ms; each sample is stamped with the host
+    time it arrived.  Start it before the warm-up (`wait_first` waits for the
+    first sample), bracket the timed region with `mark_start` / `mark_end`
+    (which waits for one sample after the region); the summary uses the
+    samples within 0.25 s of the region, so a region shorter than the
+    sampling period still gets the samples on either side of it, taken while
+    the warm-up or the region kept the GPU busy."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
         self._t = None
+        self.t0 = None
+        self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except OSError:
@@ -159,7 +171,22 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def _wait_until(self, cond, timeout: float):
+        t_end = time.perf_counter() + timeout
+        while self.proc is not None and not cond() and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
+    def wait_first(self, timeout: float = 5.0):
+        self._wait_until(lambda: len(self.lines) > 0, timeout)
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
+        self._wait_until(lambda: any(t > self.t1 for t, _ in self.lines), 3 * self.PERIOD_MS / 1e3 + 1.0)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -174,7 +201,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo = (self.t0 if self.t0 is not None else -1e30) - 0.25
+        hi = (self.t1 if self.t1 is not None else 1e30) + 0.25
+        for t, ln in self.lines:
+            if not (lo <= t <= hi):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -211,8 +242,11 @@ def kernel_source_sha1() -> str:
     return hashlib.sha1(src.encode()).hexdigest()
 
 
-def measured_traffic(stage: str, n_total: int):
-    """roofline.traffic of the given stage, or None once the kernel code changed."""
+def measured_traffic(stage: str, n_total: int, workload: str = "c2"):
+    """roofline.traffic of the given stage on the captured workload (C2), or
+    None for another workload or once the kernel code changed."""
+    if workload != MEASURED_TRAFFIC["workload"]:
+        return None
     try:
         sha = kernel_source_sha1()
     except OSError:
@@ -476,7 +510,8 @@ def main(argv=None):
                  "cells_per_point": cpp}
 
     # ---- batched: the timed step
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
+        clk.wait_first()
         for _ in range(args.warmup):
             plan.build_batched(x_dev, off, r, k, stream=stream)
         st = plan.last_status(stream)
@@ -486,12 +521,13 @@ def main(argv=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         barrier(pg)
         torch.cuda.synchronize(dev)
-        with ClockSampler(local) as clk:
-            ev[0].record(stream)
-            for i in range(args.steps):
-                plan.build_batched(x_dev, off, r, k, stream=stream)
-                ev[i + 1].record(stream)
-            torch.cuda.synchronize(dev)
+        clk.mark_start()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            plan.build_batched(x_dev, off, r, k, stream=stream)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        clk.mark_end()
         barrier(pg)
     st = plan.last_status(stream)
     if st != 0:
@@ -642,6 +678,7 @@ def main(argv=None):
     # derived from the SM count, 128 FP32 lanes per SM, two operations per
     # lane per packed f32x2 instruction, and the maximum SM clock
     alu = None
+    issue = None
     if rank == 0:
         g_used, s_used = plan.get_tuning()
         mean_cand, g_grid = host_candidates(x_host[off[0]:off[1]], r, g_used, s_used, cpp)
@@ -653,6 +690,15 @@ def main(argv=None):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_tops = n_sm * 128 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks["sm_max_mhz"] else None
         achieved_tops = ops / (total_ms_max / args.steps / 1e3) / 1e12
+        if (dom == MEASURED_TRAFFIC["stage"] and measured_traffic(dom, n_total, args.workload) is not None
+                and clocks["sm_max_mhz"]):
+            instr = MEASURED_INSTR_PER_QUERY * n_total
+            peak_g = 4 * n_sm * clocks["sm_max_mhz"] * 1e6 / 1e9
+            ach_g = instr / (stage_avg[dom] / 1e3) / 1e9
+            issue = {"warp_instructions_per_launch": instr, "achieved_g_per_s": ach_g, "peak_g_per_s": peak_g,
+                     "frac": ach_g / peak_g,
+                     "note": "instructions per query from the ncu capture of the same kernel code, scaled to this "
+                             "launch; peak = 4 warp instructions per cycle per SM x SMs x max SM clock"}
         alu = {"candidate_tests_per_step": evals, "mean_candidates_per_query": mean_cand,
                "gridded_dims": g_grid, "long_row_fraction": long_frac,
                "candidate_tests_per_s": evals / (total_ms_max / args.steps / 1e3),
@@ -688,13 +734,13 @@ def main(argv=None):
             "stages_ms": stage_avg,
             "roofline": {"bound": "hbm", "kernel": "k_" + dom,
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": measured_traffic(dom, n_total), "peak_kind": peak_kind,
+                         "traffic": measured_traffic(dom, n_total, args.workload), "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": sbytes[dom],
                          "launch_ms": stage_avg[dom],
                          "whole_build": {"algorithmic_bytes": whole_bytes,
                                          "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
                                          "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak},
-                         "alu_view": alu},
+                         "alu_view": alu, "issue_view": issue},
             "e2e": e2e,
             "labeling": labeling,
             "knn": knn,
@@ -702,7 +748,7 @@ def main(argv=None):
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_BUILD * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
-                       "reasons": clocks["reasons"]},
+                       "reasons": clocks["reasons"], "samples": clocks["samples"]},
         }
         print(json.dumps(line), flush=True)
     plan.close()
