@@ -51,10 +51,10 @@ L2_BYTES = 126 * 1024 * 1024
 # kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 # warp instructions per query of the collect walk in the same ncu capture as
-# MEASURED_TRAFFIC (1.302 G instructions for 4.8 M queries)
-MEASURED_INSTR_PER_QUERY = 1_302_432_867 / 4_800_000
+# MEASURED_TRAFFIC (1.409 G instructions for 4.8 M queries)
+MEASURED_INSTR_PER_QUERY = 1_408_751_154 / 4_800_000
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "df2858e41ee7", "bytes_per_point": 435_600_384 / 4_800_000}
+MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "7ccd436cbd72", "bytes_per_point": 438_737_664 / 4_800_000}
 
 
 def parse_args(argv=None):

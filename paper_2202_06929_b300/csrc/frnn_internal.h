@@ -15,7 +15,7 @@ constexpr int kScanItems = 8;                                  // cell scan: 204
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kRowScanItems = 2;                               // row scan: 512 points per tile (it also
 constexpr int kRowScanTile = kScanThreads * kRowScanItems;     // copies their rows: more tiles, more warps)
-constexpr int kWalkThreads = 256;   // count walk: 8 warps, 32 queries per warp at a time
+constexpr int kWalkThreads = 128;   // collect walk: 4 warps, 32 queries per warp at a time
 constexpr int kFillThreads = 128;   // fill walk: 4 warps (more shared memory per warp)
 constexpr int kMaxDimCells = 32768; // cells along one hashed dimension (float32 key bound)
 

@@ -1321,7 +1321,7 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 // are also collected, sorted, cut at k and written to the pool (space taken
 // per chunk from a counter), so that stage 7 only copies them.
 template <int DP4>
-__global__ void __launch_bounds__(kWalkThreads, DP4 <= 4 ? 3 : 1) k_walk_collect(DevState st)
+__global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2) k_walk_collect(DevState st)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
