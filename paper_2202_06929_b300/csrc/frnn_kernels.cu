@@ -1509,7 +1509,7 @@ __device__ __forceinline__ void emit_row_out(const DevState& st, unsigned long l
 // keeps its k smallest keys in its own buffer of `cap` keys with a running
 // threshold (with no cap: every neighbour, written in candidate order).
 template <int DP4>
-__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_emit(DevState st, int cap)
+__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(DevState st, int cap)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
@@ -1707,7 +1707,7 @@ __global__ void __launch_bounds__(kPtThreads) k_knn_rows(DevState st)
 // ((rho - 1/64) s)^2 (1 - 2^-10); when the rings cover the whole grid, every
 // point has been seen.
 template <int DP4>
-__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 6 : 2) k_walk_knn(DevState st, int cap)
+__global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(DevState st, int cap)
 {
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
