@@ -187,6 +187,18 @@ int launch(frnn_plan* p, int dp4, int cap, cudaStream_t s, cudaEvent_t* stage_ev
     return cudaGraphLaunch(ge->exec, s) == cudaSuccess ? FRNN_OK : FRNN_ERR_CUDA;
 }
 
+// Points per chunk of the per-point kernels: the smallest power of two from
+// kChunkMin that leaves at most about two chunks per block of those kernels,
+// up to kChunk (a single event spreads over every SM; big batches keep the
+// per-chunk overhead low).
+int chunk_points(const frnn_plan* p, long long n_total)
+{
+    const long long want = 2ll * p->base_cfg.grid_pt;
+    int c = kChunkMin;
+    while (c < kChunk && (n_total + c - 1) / c > want) c *= 2;
+    return c;
+}
+
 int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
                      int d, float r, int k, frnn_csr* out, long long* n_total)
 {
@@ -237,10 +249,11 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     CallHdr* h = reinterpret_cast<CallHdr*>(p->h_call[slot]);
     EvDesc* ev = reinterpret_cast<EvDesc*>(p->h_call[slot] + sizeof(CallHdr));
     const int cpp = p->prm.cells_per_point;
+    const int chunk = chunk_points(p, n_total);
     int chunks = 0;
     for (int b = 0; b < n_events; ++b) {
         const long long nb = ev_off[b + 1] - ev_off[b];
-        const int nc = nb > 0 ? (int)((nb + kChunk - 1) / kChunk) : 1;
+        const int nc = nb > 0 ? (int)((nb + chunk - 1) / chunk) : 1;
         ev[b].pt_off = ev_off[b];
         ev[b].n = (int)nb;
         ev[b].chunk_off = chunks;
@@ -253,6 +266,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->n_total = n_total;
     h->n_events = n_events;
     h->total_chunks = chunks;
+    h->chunk = chunk;
     h->d = d;
     h->dp = (d + 3) & ~3;
     h->k = (k == FRNN_NO_CAP) ? 0x7fffffff : k;
@@ -521,11 +535,12 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     CallHdr* h = reinterpret_cast<CallHdr*>(p->h_call[slot]);
     EvDesc* ev = reinterpret_cast<EvDesc*>(p->h_call[slot] + sizeof(CallHdr));
     const int cpp = p->prm.cells_per_point;
+    const int chunk = chunk_points(p, n_total);
     int chunks = 0;
     long long e0 = 0;
     for (int b = 0; b < n_events; ++b) {
         const long long nb = ev_off[b + 1] - ev_off[b];
-        const int nc = nb > 0 ? (int)((nb + kChunk - 1) / kChunk) : 1;
+        const int nc = nb > 0 ? (int)((nb + chunk - 1) / chunk) : 1;
         ev[b].pt_off = ev_off[b];
         ev[b].n = (int)nb;
         ev[b].chunk_off = chunks;
@@ -540,6 +555,7 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     h->n_total = n_total;
     h->n_events = n_events;
     h->total_chunks = chunks;
+    h->chunk = chunk;
     h->d = d;
     h->dp = (d + 3) & ~3;
     h->k = k;

@@ -8,7 +8,8 @@ namespace frnn {
 constexpr int kMaxG = 6;            // most gridded dimensions (3^(g-1) runs per cell)
 constexpr int kMaxRuns = 243;       // 3^(kMaxG - 1)
 constexpr int kMaxDims = 64;        // largest embedding dimension
-constexpr int kChunk = 2048;        // points per chunk of the per-point kernels
+constexpr int kChunk = 2048;        // points per chunk of the per-point kernels, at most
+constexpr int kChunkMin = 256;      // ... and at least (small builds: more chunks than blocks)
 constexpr int kPtThreads = 256;     // threads of the per-point kernels
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;                                  // cell scan: 2048 cells per tile
@@ -29,7 +30,8 @@ struct CallHdr {
     const float* emb;    // device [n_total][d], caller-owned
     long long n_total;   // points of the call
     int n_events;
-    int total_chunks;    // sum over events of max(1, ceil(n_b / kChunk))
+    int total_chunks;    // sum over events of max(1, ceil(n_b / chunk))
+    int chunk;           // points per chunk of the per-point kernels (kChunkMin .. kChunk)
     int d;
     int dp;              // row length of the sorted copy (d rounded up to 4)
     int k;               // neighbour cap

@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
         }
         if (threadIdx.x == 0) s_nf = 0;
         __syncthreads();
-        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long first = (long long)(c - e.chunk_off) * h.chunk;
         const long long rem = (long long)e.n - first;
-        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
         const float* base = h.emb + (e.pt_off + first) * D;
         const int nel = np * D;
         bool nf = false;
@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_key_hist(DevState st)
         if (threadIdx.x == 0) s_pl = st.plan[b];
         __syncthreads();
         const EvPlan& pl = s_pl;
-        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long first = (long long)(c - e.chunk_off) * h.chunk;
         const long long rem = (long long)e.n - first;
-        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
         for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
             float xv[kPtBatch][kMaxG];
 #pragma unroll
@@ -836,9 +836,9 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
         const int cell_off = st.plan[b].cell_off;
-        const long long first = (long long)(c - e.chunk_off) * kChunk;
+        const long long first = (long long)(c - e.chunk_off) * h.chunk;
         const long long rem = (long long)e.n - first;
-        const int np = (int)(rem < 0 ? 0 : (rem > kChunk ? kChunk : rem));
+        const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
         for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
             unsigned cid[kPtBatch], rk[kPtBatch];
 #pragma unroll

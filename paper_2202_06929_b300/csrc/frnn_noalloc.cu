@@ -222,6 +222,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     h.n_total = n;
     h.n_events = 1;
     h.total_chunks = (int)((n + kChunk - 1) / kChunk);
+    h.chunk = kChunk;
     h.d = d;
     h.dp = dp4 * 4;
     h.k = k_max;
