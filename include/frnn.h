@@ -259,8 +259,31 @@ FRNN_API int frnn_knn_graph_batched(frnn_plan* plan, const float* emb, const int
  * plan's kernels since the last call (FRNN_OK if none).  If several errors
  * were latched the most severe is returned, in the order TIMEOUT, OVERFLOW,
  * NONFINITE_INPUT.  A CUDA error on the stream returns FRNN_ERR_CUDA.
+ *
+ * TIMEOUT: one of the scans' waits for a preceding tile (each bounded to
+ * 2^22 polls and 1 s) ran out, so cell or row offsets of that build may be
+ * wrong.  The bit stays latched until this call reads it; until then every
+ * kernel that addresses memory through those offsets (scatter, walks, row
+ * copy, labeling, edge features) skips its work, so no access leaves the
+ * plan's buffers: a radius build returns empty rows (row_ptr all 0), a kNN
+ * build rows of unspecified content, labeling one component per point.  On
+ * reporting TIMEOUT this call restores the plan's between-builds device
+ * state (the next build is exact again) and forgets the last build
+ * (frnn_label_components and frnn_edge_features then return INVALID_ARG
+ * until the next build).
  */
 FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
+
+/*
+ * Failure-detection test hook.  The next build that launches kernels on
+ * `plan` (radius or kNN) runs its cell scan with tile 0 waiting for a
+ * predecessor that never publishes, so every tile's bounded wait runs out
+ * (after about 1 s) and FRNN_ERR_TIMEOUT is latched as described at
+ * frnn_get_last_status().  No GPU fault, trap or unbounded wait is involved:
+ * the waits end, the kernels return, the context stays usable.  Not for
+ * production use.  Errors: INVALID_ARG (NULL plan).
+ */
+FRNN_API int frnn_plan_test_stall_next_build(frnn_plan* plan);
 
 /*
  * Build the graph of one event without allocating any device memory.  The

@@ -35,6 +35,7 @@ ABI_FUNCTIONS = (
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
     "frnn_label_components", "frnn_edge_features", "frnn_knn_graph_batched",
+    "frnn_plan_test_stall_next_build",
 )
 
 
@@ -104,6 +105,7 @@ def load():
     lib.frnn_label_components.argtypes = [vp, f32, vp, vp]
     lib.frnn_edge_features.argtypes = [vp, vp, i64, i64, vp, vp]
     lib.frnn_get_last_status.argtypes = [vp, vp]
+    lib.frnn_plan_test_stall_next_build.argtypes = [vp]
     lib.frnn_status_string.argtypes = [i32]
     lib.frnn_status_string.restype = ctypes.c_char_p
     lib.frnn_version.argtypes = []
@@ -382,6 +384,11 @@ class Plan:
 
     def check(self, stream=None) -> None:
         _check(self.last_status(stream), "device status")
+
+    def test_stall_next_build(self) -> None:
+        """frnn_plan_test_stall_next_build: the next build's scan waits run out
+        (bounded, about 1 s) and latch FRNN_ERR_TIMEOUT; for failure-detection tests."""
+        _check(load().frnn_plan_test_stall_next_build(self._h), "frnn_plan_test_stall_next_build")
 
 
 def plan_bytes(n_max: int, d_max: int, k_max_cap: int, events_max: int = 1, edge_capacity: int = 0,

@@ -80,6 +80,7 @@ struct frnn_plan {
     frnn_csr last{};
     float last_r2 = 0.f;
     bool has_last = false;
+    bool stall_next = false;  // frnn_plan_test_stall_next_build
 };
 
 namespace {
@@ -276,6 +277,8 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->cell_scale = p->tuning.cell_scale;
     h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
     h->knn = 0;
+    h->stall = p->stall_next ? 1 : 0;
+    p->stall_next = false;
     h->edge_capacity = p->edge_cap;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -565,6 +568,8 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     h->cell_scale = p->tuning.cell_scale;
     h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
     h->knn = 1;
+    h->stall = p->stall_next ? 1 : 0;
+    p->stall_next = false;
     h->edge_capacity = p->edge_cap;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -686,6 +691,13 @@ int frnn_edge_features(frnn_plan* p, const float* emb, int64_t e_begin, int64_t 
     return launch_edge_features(p->st, emb, e_begin, e_end, out, p->n_sm * 8, stream) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
 }
 
+int frnn_plan_test_stall_next_build(frnn_plan* p)
+{
+    if (!p) return FRNN_ERR_INVALID_ARG;
+    p->stall_next = true;
+    return FRNN_OK;
+}
+
 int frnn_get_last_status(frnn_plan* p, void* stream)
 {
     if (!p) return FRNN_ERR_INVALID_ARG;
@@ -703,9 +715,11 @@ int frnn_get_last_status(frnn_plan* p, void* stream)
         return FRNN_ERR_CUDA;
     }
     if (word & kStTimeout) {
-        // a wait gave up part-way: restore the between-builds state
+        // a wait gave up part-way: restore the between-builds state; the last
+        // graph is not valid, so labeling and edge features refuse it
         reset_device_state(p, s);
         cudaStreamSynchronize(s);
+        p->has_last = false;
         return FRNN_ERR_TIMEOUT;
     }
     if (word & kStOverflow) return FRNN_ERR_OVERFLOW;

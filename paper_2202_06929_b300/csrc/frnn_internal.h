@@ -41,6 +41,8 @@ struct CallHdr {
     float cell_scale;    // tuning: cell edge / r (>= 1)
     int emit_d2;
     int knn;             // 1: k nearest with no radius (cell edge from density; r unused)
+    int stall;           // 1: the cell scan's first tile waits for a predecessor that never
+                         // publishes, so its bounded waits run out (failure-detection tests)
     long long edge_capacity;
 };
 
@@ -107,6 +109,16 @@ struct DevState {
     int* edge_off;           // [events_max + 1]
     unsigned* status;
 };
+
+#ifdef __CUDACC__
+// A bounded wait of this build, or of an earlier one whose status has not
+// been read yet, ran out: cell and row offsets may be wrong, so the kernels
+// that address memory through them skip their work.
+__device__ __forceinline__ bool timed_out(const DevState& st)
+{
+    return (__ldcg(st.status) & kStTimeout) != 0u;
+}
+#endif
 
 struct LaunchCfg {
     int grid_pt;       // per-point kernels (persistent: blocks loop over chunks)

@@ -44,7 +44,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kCellMargin = 1.0f + 1.0f / 64.0f;  // cell edge >= r * (1 + 2^-6)
-constexpr int kSpinLimit = 1 << 22;                 // bounded waits in the scans
+constexpr int kSpinLimit = 1 << 22;                 // polls of one bounded wait in the scans, at most
+constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and at most 1 s of it
 
 // Order-preserving map float -> uint32 (for atomicMin / atomicMax).
 __device__ __forceinline__ unsigned f2ord(float f)
@@ -55,6 +56,13 @@ __device__ __forceinline__ unsigned f2ord(float f)
 __device__ __forceinline__ float ord2f(unsigned u)
 {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
@@ -485,11 +493,17 @@ constexpr unsigned long long kFlagPre = 2ull << 62;
 // inclusive prefix ends the walk; the tiles above it add their aggregates.
 // (With hundreds of tiles in flight a 32-wide window needs many rounds of L2
 // latency per tile, and those rounds bounded the scans' throughput.)  Every
-// thread returns the same prefix.
-__device__ unsigned block_lookback(unsigned long long* state, int tile, unsigned* status)
+// thread returns the same prefix.  A wait that outlasts kSpinLimit polls or
+// kWaitNs latches kStTimeout and returns the prefix gathered so far (the
+// decision is thread 0's, shared through s_stop, so the block leaves
+// together).  before0: the state read for tiles before tile 0 (an inclusive
+// prefix of 0; a state that never becomes ready when a test stalls the scan).
+__device__ unsigned block_lookback(unsigned long long* state, int tile, unsigned* status,
+                                   unsigned long long before0)
 {
     __shared__ int s_first[32];
     __shared__ unsigned s_part[32];
+    __shared__ int s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (int)(blockDim.x >> 5);
     constexpr int kNone = 0x7fffffff;
@@ -498,13 +512,21 @@ __device__ unsigned block_lookback(unsigned long long* state, int tile, unsigned
     for (;;) {
         const int idx = top - (int)threadIdx.x;
         unsigned long long s = 0;
-        int spins = 0;
-        for (;;) {
-            s = (idx >= 0) ? ld_relaxed(state + idx) : kFlagPre;  // before tile 0: prefix 0
+        unsigned long long t0 = 0;
+        for (int spins = 0;; ++spins) {
+            s = (idx >= 0) ? ld_relaxed(state + idx) : before0;
             if (__syncthreads_and((s >> 62) != 0)) break;
-            if (++spins > kSpinLimit) {  // uniform across the block
-                if (threadIdx.x == 0) atomicOr(status, kStTimeout);
-                return prefix;
+            if ((spins & 63) == 0) {
+                if (threadIdx.x == 0) {
+                    const unsigned long long now = global_ns();
+                    if (spins == 0) t0 = now;
+                    s_stop = spins >= kSpinLimit || now - t0 > kWaitNs;
+                }
+                __syncthreads();
+                if (s_stop) {
+                    if (threadIdx.x == 0) atomicOr(status, kStTimeout);
+                    return prefix;
+                }
             }
             __nanosleep(32);
         }
@@ -599,6 +621,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         tile_ctr = &st.counters[kCtrScanRowsTile];
         exit_ctr = &st.counters[kCtrScanRowsExit];
     }
+    // The row scan of a build whose cell scan timed out sees no entries: its
+    // rows come out empty and nothing is copied.
+    const long long M_in = (MODE == 1 && timed_out(st)) ? 0 : M;
+    const bool stall = MODE == 0 && st.hdr->stall != 0;
     const long long nsub = (M + SUB - 1) / SUB;
     const long long spt = (nsub + gridDim.x - 1) / gridDim.x;  // sub-tiles per tile
     const int ntiles = (int)(spt > 0 ? (nsub + spt - 1) / spt : 0);
@@ -614,25 +640,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
 #pragma unroll 4
         for (long long sb = sub0; sb < sub1; ++sb) {
             unsigned v[IT];
-            scan_load<MODE, IT>(in, sb * SUB + (long long)threadIdx.x * IT, M, false, v);
+            scan_load<MODE, IT>(in, sb * SUB + (long long)threadIdx.x * IT, M_in, false, v);
 #pragma unroll
             for (int i = 0; i < IT; ++i) tsum += v[i];
         }
         unsigned total;
         block_excl_scan(tsum, &total);
         unsigned prefix = 0;
-        if (tile == 0) {
+        if (tile == 0 && !stall) {
             if (threadIdx.x == 0) st_relaxed(state, kFlagPre | total);
         } else {
             if (threadIdx.x == 0) st_relaxed(state + tile, kFlagAgg | total);
-            prefix = block_lookback(state, tile, st.status);
+            prefix = block_lookback(state, tile, st.status, stall ? 0ull : kFlagPre);
             if (threadIdx.x == 0) st_relaxed(state + tile, kFlagPre | (unsigned)(prefix + total));
         }
         // second pass: scan the sub-tiles in order
         for (long long sb = sub0; sb < sub1; ++sb) {
             const long long base = sb * SUB + (long long)threadIdx.x * IT;
             unsigned v[IT];
-            scan_load<MODE, IT>(in, base, M, true, v);
+            scan_load<MODE, IT>(in, base, M_in, true, v);
             int po[IT];  // row scan: pool slots (they do not depend on the scan)
 #pragma unroll
             for (int i = 0; i < IT; ++i) po[i] = (MODE == 1 && base + i < M) ? __ldg(st.pool_off + base + i) : -1;
@@ -828,6 +854,7 @@ __device__ __forceinline__ void copy_row(const float* x, float4* dst, int D, int
 
 __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 {
+    if (timed_out(st)) return;
     const CallHdr h = *st.hdr;
     const int D = h.d, dp = h.dp;
     const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
@@ -1323,6 +1350,7 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 template <int DP4>
 __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2) k_walk_collect(DevState st)
 {
+    if (timed_out(st)) return;
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
@@ -1511,6 +1539,7 @@ __device__ __forceinline__ void emit_row_out(const DevState& st, unsigned long l
 template <int DP4>
 __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(DevState st, int cap)
 {
+    if (timed_out(st)) return;
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
@@ -1709,6 +1738,7 @@ __global__ void __launch_bounds__(kPtThreads) k_knn_rows(DevState st)
 template <int DP4>
 __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(DevState st, int cap)
 {
+    if (timed_out(st)) return;
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;

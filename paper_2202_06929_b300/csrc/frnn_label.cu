@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* 
     const long long P = st.hdr->n_total;
     const int B = st.hdr->n_events;
     const long long ecap = st.hdr->edge_capacity;
+    const bool dead = timed_out(st);  // the build's edges are not valid: every point alone
     long long lo = 1, hi = 0, off = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         if (p < lo || p >= hi) {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_init(DevState st, int* 
         }
         const int rs = st.row_ptr[p], re = st.row_ptr[p + 1];
         long long m = p;
-        if ((long long)re <= ecap) {
+        if (!dead && (long long)re <= ecap) {
             for (int e = rs; e < re; ++e) {
                 if (use_d2 && !(st.d2[e] <= d2_max)) continue;
                 const int c = st.col[e];
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kLabelThreads) k_label_compress(DevState st, i
 // edge whose far end already hangs directly under it costs one load.
 __global__ void __launch_bounds__(kLabelThreads) k_label_union(DevState st, int* parent, float d2_max, int use_d2)
 {
+    if (timed_out(st)) return;
     const bool any_capped = __ldcg(&st.counters[kCtrLabelCapped]) != 0u;
     const long long P = st.hdr->n_total;
     const int B = st.hdr->n_events;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kLabelThreads) k_edge_features(DevState st, co
     const int B = st.hdr->n_events;
     const int D = st.hdr->d;
     const int W = 2 * D + 1;
-    if (P == 0 || e_end <= e_begin) return;
+    if (P == 0 || e_end <= e_begin || timed_out(st)) return;
     const long long p_lo = row_of_edge(st.row_ptr, P, e_begin);
     const long long p_hi = row_of_edge(st.row_ptr, P, e_end - 1);
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
