@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
             unsigned mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mn3 = 0xffffffffu;
             unsigned mx0 = 0u, mx1 = 0u, mx2 = 0u, mx3 = 0u;
             if ((int)threadIdx.x < S) {
-#pragma unroll 4
+#pragma unroll 8
                 for (int i = threadIdx.x; i < n4; i += S) {
                     const float4 v = __ldg(b4 + i);
                     nf |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
@@ -377,9 +377,11 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
             }
         }
         if (threadIdx.x == 0 && s_nf) atomicOr(&st.nonfinite[b], 1u);
-        __threadfence();
+        // the barrier orders every thread's atomics before thread 0's fence,
+        // which publishes them before the chunk is counted
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             const unsigned done = atomicAdd(&st.chunk_done[b], 1u);
             s_last = (done == (unsigned)e.nchunk - 1u);
         }
@@ -654,14 +656,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
             prefix = block_lookback(state, tile, st.status, stall ? 0ull : kFlagPre);
             if (threadIdx.x == 0) st_relaxed(state + tile, kFlagPre | (unsigned)(prefix + total));
         }
-        // second pass: scan the sub-tiles in order
+        // second pass: scan the sub-tiles in order, each one's loads issued
+        // before the previous one is scanned
+        unsigned vn[IT];
+        int pon[IT];  // row scan: pool slots (they do not depend on the scan)
+        auto load_sub = [&](long long sb) {
+            const long long b0 = sb * SUB + (long long)threadIdx.x * IT;
+            scan_load<MODE, IT>(in, b0, M_in, true, vn);
+#pragma unroll
+            for (int i = 0; i < IT; ++i) pon[i] = (MODE == 1 && b0 + i < M) ? __ldg(st.pool_off + b0 + i) : -1;
+        };
+        if (sub0 < sub1) load_sub(sub0);
         for (long long sb = sub0; sb < sub1; ++sb) {
             const long long base = sb * SUB + (long long)threadIdx.x * IT;
             unsigned v[IT];
-            scan_load<MODE, IT>(in, base, M_in, true, v);
-            int po[IT];  // row scan: pool slots (they do not depend on the scan)
+            int po[IT];
 #pragma unroll
-            for (int i = 0; i < IT; ++i) po[i] = (MODE == 1 && base + i < M) ? __ldg(st.pool_off + base + i) : -1;
+            for (int i = 0; i < IT; ++i) {
+                v[i] = vn[i];
+                po[i] = pon[i];
+            }
+            if (sb + 1 < sub1) load_sub(sb + 1);
             unsigned ssum = 0;
 #pragma unroll
             for (int i = 0; i < IT; ++i) ssum += v[i];
@@ -867,6 +882,17 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const long long rem = (long long)e.n - first;
         const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
         for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
+            // D = 8 (rows of 32 bytes, the input 32-byte aligned): one 32-byte
+            // load per row, issued with the key and rank loads, before the
+            // cell-table loads that depend on them
+            F8 row[kPtBatch];
+            if (vec8) {
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
+                }
+            }
             unsigned cid[kPtBatch], rk[kPtBatch];
 #pragma unroll
             for (int u = 0; u < kPtBatch; ++u) {
@@ -879,14 +905,6 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 #pragma unroll
             for (int u = 0; u < kPtBatch; ++u) pos[u] = (long long)__ldg(st.cell_start + cell_off + cid[u]) + rk[u];
             if (vec8) {
-                // D = 8 (rows of 32 bytes, the input 32-byte aligned): one
-                // 32-byte load and store per row, all loads before any store
-                F8 row[kPtBatch];
-#pragma unroll
-                for (int u = 0; u < kPtBatch; ++u) {
-                    const int i = i0 + u * kPtThreads;
-                    row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
-                }
 #pragma unroll
                 for (int u = 0; u < kPtBatch; ++u) {
                     const int i = i0 + u * kPtThreads;
