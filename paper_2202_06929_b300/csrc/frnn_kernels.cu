@@ -1350,8 +1350,8 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
 }
 
 // Rows with |S_i| <= kFast are kept whole by the collect walk (one slot per
-// key in shared memory) and sorted there; longer rows are left to the emit
-// walk, which selects the k smallest keys on its own.
+// key in shared memory) and placed in sorted order from there; longer rows
+// are left to the emit walk, which selects the k smallest keys on its own.
 constexpr int kChunkGroup = 2;  // consecutive chunks a warp takes at a time
 constexpr int kRowSlots = kFast + 1;   // a row also holds the query's own key while collecting
 constexpr int kRowStride = kFast + 1;  // = kRowSlots; odd, so row starts of lanes 0..15 fall in distinct banks
@@ -1483,39 +1483,37 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
             if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
         }
         __syncwarp();
-        // every lane sorts its own row (insertion sort, at most kRowSlots keys);
-        // the query's own key (d2 = 0, j = itself) is set to the largest value
-        // first, so that it sorts last and the first |S_i| keys are the row ...
-        if (my_off >= 0) {
-            unsigned long long* row = keys + lane * kRowStride;
-            const unsigned long long self_key = (unsigned long long)(unsigned)self_j;
-            if (row[0] == self_key) row[0] = ~0ull;
-            for (int x = 1; x < raw; ++x) {
-                unsigned long long v = row[x];
-                if (v == self_key) v = ~0ull;
-                int y = x - 1;
-                while (y >= 0 && row[y] > v) {
-                    row[y + 1] = row[y];
-                    --y;
-                }
-                row[y + 1] = v;
-            }
-        }
-        __syncwarp();
-        // ... then the rows, cut at k, go to the pool: they fill
-        // [base_off, base_off + tot) in lane order, so the warp writes that
-        // range flat, each entry finding its row by binary lifting over the
-        // lanes' prefix sums
+        // The parked rows go to the pool sorted and cut at k: they fill
+        // [base_off, base_off + tot) in lane order.  The warp streams the
+        // rows' collected keys (the query's own key included) flat, each key
+        // finding its row by binary lifting over the lanes' prefix sums; a
+        // key's place in its row is the number of the row's keys below it,
+        // less one if the query's own key (d2 = 0, j = itself) is among them.
         if (fits) {
+            const int nin = my_off >= 0 ? raw : 0;
+            const int incl_in = warp_incl_scan(nin, lane);
+            const int tot_in = __shfl_sync(kFull, incl_in, 31);
+            const int excl_in = incl_in - nin;
             const int excl = incl - need;
-            for (int e0 = 0; e0 < tot; e0 += 32) {
+            for (int e0 = 0; e0 < tot_in; e0 += 32) {
                 const int e = e0 + lane;
-                const int L = find_run(incl, e);
-                const int exl = __shfl_sync(kFull, excl, L);
-                if (e < tot) {
-                    const unsigned long long kk = keys[L * kRowStride + (e - exl)];
-                    st.pool[base_off + e] = (int)(unsigned)kk;
-                    if (emit) st.pool_d2[base_off + e] = __uint_as_float((unsigned)(kk >> 32));
+                const int L = find_run(incl_in, e);
+                const int xin = __shfl_sync(kFull, excl_in, L);
+                const int nl = __shfl_sync(kFull, nin, L);
+                const int ol = __shfl_sync(kFull, excl, L);
+                const int cl = __shfl_sync(kFull, cnt, L);
+                const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
+                if (e < tot_in) {
+                    const unsigned long long* row = keys + L * kRowStride;
+                    const unsigned long long kk = row[e - xin];
+                    if (kk != self_key) {
+                        int rank = (self_key < kk) ? -1 : 0;
+                        for (int y = 0; y < nl; ++y) rank += row[y] < kk;
+                        if (rank < cl) {
+                            st.pool[base_off + ol + rank] = (int)(unsigned)kk;
+                            if (emit) st.pool_d2[base_off + ol + rank] = __uint_as_float((unsigned)(kk >> 32));
+                        }
+                    }
                 }
             }
         }
