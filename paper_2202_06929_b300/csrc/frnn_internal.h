@@ -122,6 +122,7 @@ __device__ __forceinline__ bool timed_out(const DevState& st)
 
 struct LaunchCfg {
     int grid_pt;       // per-point kernels (persistent: blocks loop over chunks)
+    int grid_scatter;  // scatter: as many blocks as are resident at once
     int grid_scan;     // scans (persistent: blocks take tiles from a counter)
     int grid_count;    // count walk (persistent: warps stride over queries)
     int grid_fill;     // fill walk

@@ -1996,7 +1996,7 @@ int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream
     mark(ev, 2, s);
     k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 3, s);
-    k_scatter<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_scatter<<<cfg.grid_scatter, kPtThreads, 0, s>>>(st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     switch (dp4) {
@@ -2013,7 +2013,7 @@ int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream)
     k_bbox_plan<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
     k_key_hist<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
     k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
-    k_scatter<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_scatter<<<cfg.grid_scatter, kPtThreads, 0, s>>>(st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     switch (dp4) {
@@ -2040,6 +2040,11 @@ int config_pt(int n_sm, LaunchCfg* cfg)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_key_hist, kPtThreads, 0);
     if (e != cudaSuccess) return (int)e;
     cfg->grid_pt = n_sm * (nb > 0 ? (nb < 4 ? nb : 4) : 1);
+    // the scatter keeps four 32-byte rows per thread in flight (96 registers):
+    // a second wave of blocks would only lengthen its tail
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter, kPtThreads, 0);
+    if (e != cudaSuccess) return (int)e;
+    cfg->grid_scatter = n_sm * (nb > 0 ? (nb < 4 ? nb : 4) : 1);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<0>, kScanThreads, 0);
     if (e != cudaSuccess) return (int)e;
     cfg->grid_scan = n_sm * (nb > 0 ? (nb < 4 ? nb : 4) : 1);
