@@ -48,9 +48,13 @@ constexpr int kSpinLimit = 1 << 22;                 // polls of one bounded wait
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and at most 1 s of it
 // kNN builds: cell edge as a fraction of the estimated k-th neighbour
 // distance.  Speed only (the ring walk's stop rule keeps any edge exact);
-// 0.7 was fastest or within 10% of it over k = 4, 16, 64 on 120k-point
-// 8-dim events and k = 16 on 1M-point 12-dim events (1.0 was 1.1-2.1x slower).
-constexpr float kKnnCellFactor = 0.7f;
+// with the rings' gap pruning, 0.75 was within 5-12% of the fastest factor
+// over k = 4, 16, 64 on 120k-point 8-dim events and k = 16 on 1M-point
+// 12-dim events (1.0 was up to 4x slower, 0.5 up to 3x).
+constexpr float kKnnCellFactor = 0.75f;
+// Margin (cells) on a gap between a query and a cell: each side's float32
+// cell coordinate is within 0.006 cells of (x - lo) / s.
+constexpr float kGapMargin = 1.0f / 64.0f;
 
 // Order-preserving map float -> uint32 (for atomicMin / atomicMax).
 __device__ __forceinline__ unsigned f2ord(float f)
@@ -1208,6 +1212,7 @@ __device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int2* run
 // Non-empty slots are packed into groups of at most 32 runs.
 template <typename Body>
 __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const int* cell_start, int lane,
+                                                    const float* amin, const float* amax, float prune_d2,
                                                     Body&& body)
 {
     const EvPlan& pl = ww.pl;
@@ -1225,6 +1230,7 @@ __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const
         if (si < nslot) {
             int rem = si >> 1, cb = 0, reach = 0;
             bool ok = true;
+            float lb = 0.f;  // squared lower bound on the distance to the slot's points (cell units)
             for (int t = 0; t < g - 1; ++t) {
                 const int o = rem % side - rho;
                 rem /= side;
@@ -1232,16 +1238,31 @@ __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const
                 ok &= (kt >= 0) && (kt < pl.ncell[t]);
                 cb += kt * pl.stride[t];
                 reach = max(reach, abs(o));
+                const float h = o > 0 ? (float)o - amax[t] - kGapMargin
+                              : o < 0 ? (float)(-o - 1) + amin[t] - kGapMargin : 0.f;
+                lb += h > 0.f ? h * h : 0.f;
             }
+            const float lim = prune_d2 / (pl.s * pl.s * (1.0f - 1.0f / 1024.0f));  // in cell units squared
             int c0 = 0, c1 = -1;  // fastest-dim cells of this slot
             if (reach == rho) {
-                if ((si & 1) == 0) {
-                    c0 = max(kl - rho, 0);
-                    c1 = min(kl + rho, ncl - 1);
+                if ((si & 1) == 0 && lb <= lim) {
+                    // the run k-rho .. k+rho, cut to the offsets whose gap
+                    // along the fastest dim still fits under the bound
+                    int on = rho, op = rho;
+                    if (lim < 1e30f) {
+                        const float hm = sqrtf(lim - lb);
+                        op = max(0, min(rho, (int)floorf(hm + amax[g - 1] + kGapMargin)));
+                        on = max(0, min(rho, (int)floorf(hm - amin[g - 1] + kGapMargin) + 1));
+                    }
+                    c0 = max(kl - on, 0);
+                    c1 = min(kl + op, ncl - 1);
                 }
             } else {
                 const int c = (si & 1) ? kl + rho : kl - rho;
-                if (c >= 0 && c < ncl) c0 = c1 = c;
+                const float h = (si & 1) ? (float)rho - amax[g - 1] - kGapMargin
+                                         : (float)(rho - 1) + amin[g - 1] - kGapMargin;
+                if (h > 0.f) lb += h * h;
+                if (c >= 0 && c < ncl && lb <= lim) c0 = c1 = c;
             }
             if (ok && c1 >= c0) {
                 beg = cell_start[pl.cell_off + cb + c0];
@@ -1777,6 +1798,7 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
     const int emit = st.hdr->emit_d2;
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
     __shared__ WarpWalk s_ww[kFillThreads / 32];
+    __shared__ float s_amin[kFillThreads / 32][kMaxG], s_amax[kFillThreads / 32][kMaxG];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
     for (;;) {
@@ -1825,6 +1847,17 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
             }
             __syncwarp();
             segment_cell(ww, sq, 0, lane);
+            // the pair's offsets within its cell along the gridded dims, in
+            // cells (the smaller and the larger of the two queries')
+            if (lane < ww.pl.g) {
+                const int t = ww.pl.dims[lane];
+                const float k = (float)ww.ks[lane];
+                const float a0 = __fmul_rn(__fsub_rn(sq[2 * t], ww.pl.lo[lane]), ww.pl.inv_s) - k;
+                const float a1 = __fmul_rn(__fsub_rn(sq[2 * t + 1], ww.pl.lo[lane]), ww.pl.inv_s) - k;
+                s_amin[wib][lane] = fminf(a0, a1);
+                s_amax[wib][lane] = fmaxf(a0, a1);
+            }
+            __syncwarp();
             // rings needed to cover the grid from this cell
             int rho_max = 1;
             for (int t = 0; t < ww.pl.g; ++t)
@@ -1890,8 +1923,16 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
                     }
                     break;
                 }
-                if (rho == 1) for_each_run_group(ww, run_tab, st.cell_start, lane, batch);
-                else for_each_ring_group(ww, rho, st.cell_start, lane, batch);
+                if (rho == 1) {
+                    for_each_run_group(ww, run_tab, st.cell_start, lane, batch);
+                } else {
+                    // a slot whose points all lie farther than every open
+                    // row's k_b-th key holds none of their neighbours
+                    float prune = 0.f;
+                    if (!done0) prune = nk0 >= kb ? __uint_as_float((unsigned)(thr0 >> 32)) : __int_as_float(0x7f800000);
+                    if (!done1) prune = fmaxf(prune, nk1 >= kb ? __uint_as_float((unsigned)(thr1 >> 32)) : __int_as_float(0x7f800000));
+                    for_each_ring_group(ww, rho, st.cell_start, lane, s_amin[wib], s_amax[wib], prune, batch);
+                }
                 // keep the k_b smallest keys of each row and test its stop rule
                 const float lim = (float)rho - 1.0f / 64.0f;
                 const float cov = (lim * cs) * (lim * cs) * (1.0f - 1.0f / 1024.0f);

@@ -203,3 +203,20 @@ def test_knn_edge_features_equal_oracle():
     np.testing.assert_array_equal(feats[:, :6], x[src])
     np.testing.assert_array_equal(feats[:, 6:12], x[col])
     np.testing.assert_array_equal(feats[:, 12], d2)
+
+
+@pytest.mark.parametrize("k", [6, 18, 26, 32, 80])
+def test_knn_lattice_ties_at_shell_boundaries(k):
+    """A regular lattice in 3 of 8 dims: neighbour shells of equal d2 (6 at
+    one spacing, 12 at sqrt 2, 8 at sqrt 3, ...), so the k-th key often ties
+    with keys of several other cells and ring slots; the rings' gap pruning
+    must keep every tied candidate whose index sorts first."""
+    m = 12
+    g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1).reshape(-1, 3)
+    x = np.zeros((g.shape[0], 8), np.float32)
+    x[:, :3] = (g * 8 - 44).astype(np.float32) / 256.0  # on the 1/256 grid
+    rng = np.random.default_rng(2202069290)
+    x = x[rng.permutation(x.shape[0])]
+    host, st = knn_gpu(x, k)
+    assert st == frnn.FRNN_OK
+    assert_rows_equal(host, x, k)
