@@ -48,9 +48,10 @@ constexpr int kSpinLimit = 1 << 22;                 // polls of one bounded wait
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and at most 1 s of it
 // kNN builds: cell edge as a fraction of the estimated k-th neighbour
 // distance.  Speed only (the ring walk's stop rule keeps any edge exact);
-// with the rings' gap pruning, 0.75 was within 5-12% of the fastest factor
+// with the rings' gap pruning, 0.75 was within 0-28% of the fastest factor
 // over k = 4, 16, 64 on 120k-point 8-dim events and k = 16 on 1M-point
-// 12-dim events (1.0 was up to 4x slower, 0.5 up to 3x).
+// 12-dim events; 0.5 was up to 3x slower, and from 0.9 up the 12-dim events
+// grid fewer dims (a dim needs >= 4 cells) and ran 4x slower.
 constexpr float kKnnCellFactor = 0.75f;
 // Margin (cells) on a gap between a query and a cell: each side's float32
 // cell coordinate is within 0.006 cells of (x - lo) / s.
@@ -1213,13 +1214,26 @@ __device__ __forceinline__ void for_each_run_group(WarpWalk& ww, const int2* run
 template <typename Body>
 __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const int* cell_start, int lane,
                                                     const float* amin, const float* amax, float prune_d2,
-                                                    Body&& body)
+                                                    int* box_lo, int* box_side, Body&& body)
 {
     const EvPlan& pl = ww.pl;
     const int g = pl.g;
-    const int side = 2 * rho + 1;
+    const float lim = prune_d2 / (pl.s * pl.s * (1.0f - 1.0f / 1024.0f));  // in cell units squared
+    // per slower dim, the offsets in [-rho, rho] whose gap alone fits under
+    // the bound (a combination outside this box would be pruned anyway)
+    if (lane < g - 1) {
+        int lo_o = -rho, hi_o = rho;
+        if (lim < 1e30f) {
+            const float hm = sqrtf(lim);
+            hi_o = max(0, min(rho, (int)floorf(hm + amax[lane] + kGapMargin)));
+            lo_o = -max(0, min(rho, (int)floorf(hm - amin[lane] + kGapMargin) + 1));
+        }
+        box_lo[lane] = lo_o;
+        box_side[lane] = hi_o - lo_o + 1;
+    }
+    __syncwarp();
     int ncomb = 1;
-    for (int t = 0; t < g - 1; ++t) ncomb *= side;
+    for (int t = 0; t < g - 1; ++t) ncomb *= box_side[t];
     const int nslot = 2 * ncomb;
     const int kl = ww.ks[g - 1], ncl = pl.ncell[g - 1];
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -1232,8 +1246,8 @@ __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const
             bool ok = true;
             float lb = 0.f;  // squared lower bound on the distance to the slot's points (cell units)
             for (int t = 0; t < g - 1; ++t) {
-                const int o = rem % side - rho;
-                rem /= side;
+                const int o = box_lo[t] + rem % box_side[t];
+                rem /= box_side[t];
                 const int kt = ww.ks[t] + o;
                 ok &= (kt >= 0) && (kt < pl.ncell[t]);
                 cb += kt * pl.stride[t];
@@ -1242,7 +1256,6 @@ __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const
                               : o < 0 ? (float)(-o - 1) + amin[t] - kGapMargin : 0.f;
                 lb += h > 0.f ? h * h : 0.f;
             }
-            const float lim = prune_d2 / (pl.s * pl.s * (1.0f - 1.0f / 1024.0f));  // in cell units squared
             int c0 = 0, c1 = -1;  // fastest-dim cells of this slot
             if (reach == rho) {
                 if ((si & 1) == 0 && lb <= lim) {
@@ -1799,6 +1812,7 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
     __shared__ WarpWalk s_ww[kFillThreads / 32];
     __shared__ float s_amin[kFillThreads / 32][kMaxG], s_amax[kFillThreads / 32][kMaxG];
+    __shared__ int s_box[kFillThreads / 32][2][kMaxG];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
     for (;;) {
@@ -1931,7 +1945,8 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
                     float prune = 0.f;
                     if (!done0) prune = nk0 >= kb ? __uint_as_float((unsigned)(thr0 >> 32)) : __int_as_float(0x7f800000);
                     if (!done1) prune = fmaxf(prune, nk1 >= kb ? __uint_as_float((unsigned)(thr1 >> 32)) : __int_as_float(0x7f800000));
-                    for_each_ring_group(ww, rho, st.cell_start, lane, s_amin[wib], s_amax[wib], prune, batch);
+                    for_each_ring_group(ww, rho, st.cell_start, lane, s_amin[wib], s_amax[wib], prune, s_box[wib][0],
+                                        s_box[wib][1], batch);
                 }
                 // keep the k_b smallest keys of each row and test its stop rule
                 const float lim = (float)rho - 1.0f / 64.0f;
