@@ -1257,7 +1257,9 @@ __device__ __forceinline__ void for_each_ring_group(WarpWalk& ww, int rho, const
                 lb += h > 0.f ? h * h : 0.f;
             }
             int c0 = 0, c1 = -1;  // fastest-dim cells of this slot
-            if (reach == rho) {
+            if (reach == 0 && rho == 1) {
+                // ring 1's centre run is walked by the caller beforehand
+            } else if (reach == rho) {
                 if ((si & 1) == 0 && lb <= lim) {
                     // the run k-rho .. k+rho, cut to the offsets whose gap
                     // along the fastest dim still fits under the bound
@@ -1783,9 +1785,11 @@ __global__ void __launch_bounds__(kPtThreads) k_knn_rows(DevState st)
 }
 
 // The kNN walk.  A warp takes two consecutive points in cell order (walked
-// together when they share a cell, as in the emit walk) and visits the 3^g
-// block of cells around them, then rings of cells at Chebyshev distance
-// rho = 2, 3, ... along the gridded dims.  After ring rho every point not yet
+// together when they share a cell, as in the emit walk) and visits their own
+// run of cells, the rest of the 3^g block around them, then rings of cells at
+// Chebyshev distance rho = 2, 3, ... along the gridded dims; every visit after
+// the first skips the slots that cannot hold a neighbour (see
+// for_each_ring_group).  After ring rho every point not yet
 // visited lies at least rho - 1/64 cell edges away along some gridded dim
 // (the float32 cell coordinate is within 0.006 cells of (x - lo) / s), so a
 // query is done once it holds k_b keys and its k_b-th d2 is below
@@ -1912,7 +1916,6 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
                     __syncwarp();
                 }
             };
-            const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
             for (int rho = 1;; ++rho) {
                 // past kKnnMaxRing rings, or kKnnMaxComb offset combinations
                 // in one ring (a far outlier stretching the grid), the walk
@@ -1938,8 +1941,30 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
                     break;
                 }
                 if (rho == 1) {
-                    for_each_run_group(ww, run_tab, st.cell_start, lane, batch);
-                } else {
+                    // the pair's own run first (slower-dim offsets 0), so
+                    // that rows holding k_b keys get a threshold that prunes
+                    // the rest of the 3^g block
+                    {
+                        int cb = 0;
+                        for (int t = 0; t < ww.pl.g - 1; ++t) cb += ww.ks[t] * ww.pl.stride[t];
+                        const int kl = ww.ks[ww.pl.g - 1], ncl = ww.pl.ncell[ww.pl.g - 1];
+                        const int* cs0 = st.cell_start + ww.pl.cell_off + cb;
+                        const int beg = cs0[max(kl - 1, 0)];
+                        const int len = cs0[min(kl + 1, ncl - 1) + 1] - beg;
+                        batch(make_runs(lane == 0 ? beg : 0, lane == 0 ? len : 0, lane));
+                    }
+                    if (!done0 && nk0 >= kb) {
+                        warp_sort_smem(keys0, nk0, lane);
+                        nk0 = kb;
+                        thr0 = keys0[kb - 1];
+                    }
+                    if (!done1 && nk1 >= kb) {
+                        warp_sort_smem(keys1, nk1, lane);
+                        nk1 = kb;
+                        thr1 = keys1[kb - 1];
+                    }
+                }
+                {
                     // a slot whose points all lie farther than every open
                     // row's k_b-th key holds none of their neighbours
                     float prune = 0.f;
