@@ -45,6 +45,7 @@ def test_null_plan_and_bad_params_rejected_on_host():
     off = (ctypes.c_int64 * 2)(0, 10)
     assert lib.frnn_build_graph_batched(None, None, off, 1, 3, ctypes.c_float(0.1), 4, None, ctypes.byref(c)) == 1
     assert lib.frnn_get_last_status(None, None) == 1
+    assert lib.frnn_plan_test_stall_next_build(None) == 1
     assert lib.frnn_plan_destroy(None) == 0
     h = ctypes.c_void_p()
     assert lib.frnn_plan_create(ctypes.byref(h), None) == 1
