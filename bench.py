@@ -223,6 +223,46 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- peaks
 
+EDGE_BATCH = 800_000   # edges per filter batch (Sec. 3)
+
+
+def edge_feature_bytes(batch_edges: int, rows: int, d: int) -> int:
+    """Algorithmic bytes of one edge-feature batch: per edge the (2d + 1)
+    float32 output, its column and the neighbour's row; per row touched the
+    query's row and its row offset."""
+    return batch_edges * (4 * (2 * d + 1) + 4 + 4 * d) + rows * (4 * d + 4)
+
+
+def edge_feature_bench(plan, x_dev, csr, n_total, d, stream, dev, max_batches=20):
+    import torch
+    n_edges = csr.n_edges()
+    nb = min(n_edges // EDGE_BATCH, max_batches)
+    if nb < 1:
+        return None
+    outs = [torch.empty((EDGE_BATCH, 2 * d + 1), dtype=torch.float32, device=dev) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        plan.edge_features(x_dev, 0, EDGE_BATCH, stream=stream, out=outs[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for bi in range(nb):
+            plan.edge_features(x_dev, bi * EDGE_BATCH, (bi + 1) * EDGE_BATCH, stream=stream, out=outs[bi % 4])
+        e1.record(stream)
+        e1.synchronize()
+    if plan.last_status(stream) != 0:
+        return None
+    ms = e0.elapsed_time(e1) / nb
+    row_ptr = csr.row_ptr[: n_total + 1].cpu().numpy().astype(np.int64)
+    last = nb * EDGE_BATCH
+    rows = int(np.searchsorted(row_ptr, last, side="left"))  # rows whose edges start before the last edge timed
+    byts = edge_feature_bytes(EDGE_BATCH, max(1, rows // nb), d)
+    hbm, kind = measured_peaks()
+    gbs = byts / (ms / 1e3) / 1e9
+    return {"batch_edges": EDGE_BATCH, "batches": nb, "ms_per_batch": ms, "edges_per_s": EDGE_BATCH / (ms / 1e3),
+            "algorithmic_bytes_per_batch": byts, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm, "peak_kind": kind,
+            "note": "frnn_edge_features over the step's first edges, device time per batch; bytes per edge: "
+                    "(2d+1) float32 out + column + neighbour row; per row: its row and offset"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -563,7 +603,7 @@ def main(argv=None):
     # ---- track labeling (connected components of the built graph, every edge kept)
     labeling = None
     with torch.cuda.stream(stream):
-        plan.build_batched(x_dev, off, r, k, stream=stream)
+        csr_last = plan.build_batched(x_dev, off, r, k, stream=stream)
         lab = torch.empty(n_total, dtype=torch.int32, device=dev)
         plan.label_components(float("inf"), stream=stream, out=lab)
         le0, le1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -579,6 +619,11 @@ def main(argv=None):
         labeling = {"ms_per_step": float(np.median(lab_ms)), "components_per_step": n_tracks,
                     "note": "frnn_label_components: weakly connected components of the step's graphs "
                             "(all edges kept), 4 kernels, after the build on the same stream"}
+
+    # ---- edge features for the filter stage: [x_i, x_j, d2] per edge of the same
+    # graph, in 800k-edge batches (the filter network's batch, Sec. 3); outputs
+    # rotate over 4 buffers (218 MB, more than L2)
+    edge_features = edge_feature_bench(plan, x_dev, csr_last, n_total, d, stream, dev)
 
     # ---- exact k nearest neighbours (no radius) of the same batch
     knn = None
@@ -743,6 +788,7 @@ def main(argv=None):
                          "alu_view": alu, "issue_view": issue},
             "e2e": e2e,
             "labeling": labeling,
+            "edge_features": edge_features,
             "knn": knn,
             "served": served,
             "cpu_baseline": cpu,

@@ -79,6 +79,7 @@ struct frnn_plan {
     long long d_input_floats = 0;
     frnn_csr last{};
     float last_r2 = 0.f;
+    int last_d = 0;
     bool has_last = false;
     bool stall_next = false;  // frnn_plan_test_stall_next_build
 };
@@ -240,6 +241,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
             return FRNN_ERR_CUDA;
         p->last = *out;
         p->last_r2 = r * r;
+        p->last_d = d;
         p->has_last = true;
         return FRNN_OK;
     }
@@ -289,6 +291,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     if (rc != FRNN_OK) return rc;
     p->last = *out;
     p->last_r2 = r * r;
+    p->last_d = d;
     p->has_last = true;
     return FRNN_OK;
 }
@@ -529,6 +532,7 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
             return FRNN_ERR_CUDA;
         p->last = *out;
         p->last_r2 = inf;
+        p->last_d = d;
         p->has_last = true;
         return FRNN_OK;
     }
@@ -582,6 +586,7 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     if (launch_knn(st, h->dp / 4, cfg, s) != 0) return FRNN_ERR_CUDA;
     p->last = *out;
     p->last_r2 = inf;
+    p->last_d = d;
     p->has_last = true;
     return FRNN_OK;
 }
@@ -688,7 +693,8 @@ int frnn_edge_features(frnn_plan* p, const float* emb, int64_t e_begin, int64_t 
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
     if (e_end == e_begin || p->last.n_total == 0) return FRNN_OK;
-    return launch_edge_features(p->st, emb, e_begin, e_end, out, p->n_sm * 8, stream) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
+    return launch_edge_features(p->st, emb, p->last_d, e_begin, e_end, out, p->n_sm, stream) == 0 ? FRNN_OK
+                                                                                                : FRNN_ERR_CUDA;
 }
 
 int frnn_plan_test_stall_next_build(frnn_plan* p)

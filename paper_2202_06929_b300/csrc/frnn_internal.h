@@ -139,8 +139,8 @@ int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg);
 // n_total ints of scratch, labels receives event-local component labels.
 int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int use_d2, int grid, void* stream);
 // Edge features [x_i, x_j, d2] of edges [e_begin, e_end) of the last build (frnn_label.cu).
-int launch_edge_features(const DevState& st, const float* emb, long long e_begin, long long e_end, float* out,
-                         int grid, void* stream);
+int launch_edge_features(const DevState& st, const float* emb, int d, long long e_begin, long long e_end,
+                         float* out, int n_sm, void* stream);
 int config_pt(int n_sm, LaunchCfg* cfg);
 // The k-nearest-neighbour build (no radius): grid, fixed-length rows, ring walk.
 int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream);

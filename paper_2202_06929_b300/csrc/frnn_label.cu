@@ -204,7 +204,7 @@ int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int
 // graph's edges in fixed-size batches): for every edge e in [e_begin, e_end)
 // of the last build, out[(e - e_begin) * (2d + 1) + ...] = x_i[0..d), x_j[0..d),
 // d2(i, j), with d2 summed in dimension order, one rounding per operation (the
-// same value the build tested).  One warp per row: its records are contiguous.
+// same value the build tested).
 namespace frnn {
 namespace {
 
@@ -219,61 +219,151 @@ __device__ __forceinline__ long long row_of_edge(const int* row_ptr, long long n
     return lo;
 }
 
-__global__ void __launch_bounds__(kLabelThreads) k_edge_features(DevState st, const float* emb, long long e_begin,
+constexpr int kEfWarps = 4;  // warps per block of the edge-feature kernel
+constexpr int kEfPer = 1;    // edges per lane of a chunk (2 measured no faster)
+constexpr int kEfChunk = 32 * kEfPer;
+constexpr unsigned kAllLanes = 0xffffffffu;
+
+// row_of_edge by a whole warp: 32 probes per step narrow the range 32-fold,
+// so a search over millions of rows takes about five dependent loads.
+__device__ __forceinline__ long long warp_row_of_edge(const int* row_ptr, long long n, long long e, int lane)
+{
+    long long lo = 0, hi = n - 1;  // the answer lies in [lo, hi]; row_ptr[lo] <= e
+    while (hi - lo >= 32) {
+        const long long span = hi - lo + 1;
+        const long long pos = lo + (span * lane) / 32;  // pos of lane 0 is lo
+        const unsigned m = __ballot_sync(kAllLanes, (long long)row_ptr[pos] <= e);
+        const int k = __popc(m);  // probes 0 .. k-1 hold, the rest do not
+        const long long nlo = lo + (span * (k - 1)) / 32;
+        const long long nhi = k < 32 ? lo + (span * k) / 32 - 1 : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    const long long pos = lo + lane;
+    const unsigned m = __ballot_sync(kAllLanes, pos <= hi && (long long)row_ptr[pos] <= e);
+    return lo + __popc(m) - 1;
+}
+
+// A warp takes a contiguous range of chunks of kEfChunk edges, kEfPer per
+// lane.  The row of its first edge comes from one warp-wide search; after that
+// the row of every edge follows by binary lifting over the 32 row starts after
+// the previous chunk's last row (a per-edge search when a chunk reaches past
+// them, i.e. many empty rows).  Each lane assembles its edges' 2d + 1 values in
+// shared memory (record stride 2d + 1 is odd, so the lanes' writes hit
+// distinct banks) and the warp stores the chunk's records with consecutive
+// 4-byte writes.
+__global__ void __launch_bounds__(kEfWarps * 32) k_edge_features(DevState st, const float* emb, long long e_begin,
                                                                  long long e_end, float* out)
 {
-    const int lane = threadIdx.x & 31;
+    extern __shared__ float s_ef[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long P = st.hdr->n_total;
     const int B = st.hdr->n_events;
     const int D = st.hdr->d;
     const int W = 2 * D + 1;
+    float* buf = s_ef + (size_t)wib * kEfChunk * W;
     if (P == 0 || e_end <= e_begin || timed_out(st)) return;
-    const long long p_lo = row_of_edge(st.row_ptr, P, e_begin);
-    const long long p_hi = row_of_edge(st.row_ptr, P, e_end - 1);
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    long long lo = 1, hi = 0, off = 0;
-    for (long long p = p_lo + (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p <= p_hi; p += nwarps) {
-        if (p < lo || p >= hi) {
-            const int b = event_of(st.ev, B, p);
-            off = st.ev[b].pt_off;
-            lo = off;
-            hi = off + st.ev[b].n;
+    const long long nchunk = (e_end - e_begin + kEfChunk - 1) / kEfChunk;
+    const long long nwarps = (long long)gridDim.x * kEfWarps;
+    const long long per = (nchunk + nwarps - 1) / nwarps;
+    const long long c_begin = ((long long)blockIdx.x * kEfWarps + wib) * per;
+    const long long c_end = min(c_begin + per, nchunk);
+    if (c_begin >= c_end) return;
+    // a row at or before the chunk's first edge
+    long long p0 = warp_row_of_edge(st.row_ptr, P, e_begin + c_begin * kEfChunk, lane);
+    long long lo = 1, hi = 0, off = 0;  // this lane's event: points [lo, hi), first point off
+    for (long long c = c_begin; c < c_end; ++c) {
+        const long long e0 = e_begin + c * kEfChunk;
+        const long long e_last = min(e0 + kEfChunk - 1, e_end - 1);
+        long long e[kEfPer];
+        int cj[kEfPer];
+#pragma unroll
+        for (int u = 0; u < kEfPer; ++u) {
+            e[u] = e0 + 32 * u + lane;
+            cj[u] = e[u] < e_end ? st.col[e[u]] : 0;  // issued first: they do not depend on the rows
         }
-        const long long a = max((long long)st.row_ptr[p], e_begin);
-        const long long z = min((long long)st.row_ptr[p + 1], e_end);
-        const float* xi = emb + p * D;
-        const long long nel = (z - a) * W;
-        for (long long t = lane; t < nel; t += 32) {
-            const long long e = a + t / W;
-            const int f = (int)(t % W);
-            const int c = st.col[e];
-            const float* xj = emb + (off + (c >= 0 ? c : 0)) * D;
-            float v;
-            if (c < 0) {
-                v = __int_as_float(0x7fc00000);  // entry of an event with non-finite input: NaN features
-            } else if (f < D) {
-                v = xi[f];
-            } else if (f < 2 * D) {
-                v = xj[f - D];
-            } else {
-                float s = 0.f;
-                for (int u = 0; u < D; ++u) {
-                    const float dd = __fsub_rn(xi[u], xj[u]);
-                    s = __fadd_rn(s, __fmul_rn(dd, dd));
+        const long long pi = p0 + 1 + lane;
+        const int rs = pi <= P ? st.row_ptr[pi] : 0x7fffffff;  // starts of rows p0 + 1 ..
+        const bool lift = (long long)__shfl_sync(kAllLanes, rs, 31) > e_last;
+        long long p[kEfPer];
+#pragma unroll
+        for (int u = 0; u < kEfPer; ++u) {
+            if (lift) {
+                int r = 0;
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(kAllLanes, rs, r + step - 1);
+                    if ((long long)v <= e[u]) r += step;
                 }
-                v = s;
+                p[u] = p0 + r;
+            } else {
+                p[u] = e[u] < e_end ? row_of_edge(st.row_ptr, P, e[u]) : p0;
             }
-            out[(e - e_begin) * W + f] = v;
         }
+        {
+            // carry the row of the chunk's last edge to the next chunk
+            const int li = (int)(e_last - e0);
+            long long pl = p[0];
+#pragma unroll
+            for (int u = 1; u < kEfPer; ++u)
+                if ((li >> 5) == u) pl = p[u];
+            p0 = __shfl_sync(kAllLanes, pl, li & 31);
+        }
+#pragma unroll
+        for (int u = 0; u < kEfPer; ++u) {
+            if (e[u] >= e_end) continue;
+            if (p[u] < lo || p[u] >= hi) {
+                const int b = event_of(st.ev, B, p[u]);
+                off = st.ev[b].pt_off;
+                lo = off;
+                hi = off + st.ev[b].n;
+            }
+            float* rec = buf + (32 * u + lane) * W;
+            if (cj[u] < 0) {
+                // entry of an event with non-finite input: NaN features
+                for (int f = 0; f < W; ++f) rec[f] = __int_as_float(0x7fc00000);
+            } else {
+                const float* xi = emb + p[u] * D;
+                const float* xj = emb + (off + cj[u]) * D;
+                float sum = 0.f;
+                for (int t = 0; t < D; ++t) {
+                    const float a = __ldg(xi + t), b = __ldg(xj + t);
+                    rec[t] = a;
+                    rec[D + t] = b;
+                    const float dd = __fsub_rn(a, b);
+                    sum = __fadd_rn(sum, __fmul_rn(dd, dd));  // the build's d2: dims in order, one rounding each
+                }
+                rec[2 * D] = sum;
+            }
+        }
+        __syncwarp();
+        const int nrec = (int)(e_last - e0 + 1);
+        float* dst = out + (e0 - e_begin) * W;
+        for (int i = lane; i < nrec * W; i += 32) dst[i] = buf[i];
+        __syncwarp();  // buf is rewritten by the next chunk
     }
 }
 
 }  // namespace
 
-int launch_edge_features(const DevState& st, const float* emb, long long e_begin, long long e_end, float* out,
-                         int grid, void* stream)
+int launch_edge_features(const DevState& st, const float* emb, int d, long long e_begin, long long e_end,
+                         float* out, int n_sm, void* stream)
 {
-    k_edge_features<<<grid, kLabelThreads, 0, static_cast<cudaStream_t>(stream)>>>(st, emb, e_begin, e_end, out);
+    // one chunk's records staged per warp; the attribute covers the largest d
+    constexpr int kMaxSmem = kEfWarps * kEfChunk * (2 * kMaxDims + 1) * (int)sizeof(float);
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_edge_features, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (attr != cudaSuccess) return (int)attr;
+    if (d < 1 || d > kMaxDims) return (int)cudaErrorInvalidValue;
+    const int smem = kEfWarps * kEfChunk * (2 * d + 1) * (int)sizeof(float);
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_features, kEfWarps * 32, smem);
+    if (e != cudaSuccess) return (int)e;
+    const long long chunks = (e_end - e_begin + kEfChunk - 1) / kEfChunk;
+    long long grid = (long long)n_sm * (nb > 0 ? nb : 1);
+    const long long need = (chunks + kEfWarps - 1) / kEfWarps;
+    if (grid > need) grid = need > 0 ? need : 1;
+    k_edge_features<<<(unsigned)grid, kEfWarps * 32, smem, static_cast<cudaStream_t>(stream)>>>(st, emb, e_begin,
+                                                                                               e_end, out);
     return (int)cudaGetLastError();
 }
 

@@ -60,3 +60,12 @@ def test_stage_bytes_total_matches_whole_build_terms():
     b = bench.stage_bytes(1000, 5000, 8)
     assert b["walk_collect"] == 4 * 1000 * 8 + 12 * 1000 + 4 * 5000
     assert b["scan_rows"] == 12 * 1000 + 8 * 5000
+
+
+def test_edge_feature_bytes_counts_outputs_columns_and_rows():
+    # per edge: (2d + 1) float32 outputs, its column, the neighbour's row;
+    # per row: the query's row and its offset
+    d = 8
+    assert bench.edge_feature_bytes(1, 0, d) == 4 * 17 + 4 + 32
+    assert bench.edge_feature_bytes(800_000, 70_000, d) == 800_000 * 104 + 70_000 * 36
+    assert bench.edge_feature_bytes(0, 5, 12) == 5 * 52
