@@ -348,9 +348,10 @@ __global__ void __launch_bounds__(kEfWarps * 32) k_edge_features(DevState st, co
 int launch_edge_features(const DevState& st, const float* emb, int d, long long e_begin, long long e_end,
                          float* out, int n_sm, void* stream)
 {
-    // one chunk's records staged per warp; the attribute covers the largest d
+    // one chunk's records staged per warp; the attribute (set on the current
+    // device at every call, a host-side update) covers the largest d
     constexpr int kMaxSmem = kEfWarps * kEfChunk * (2 * kMaxDims + 1) * (int)sizeof(float);
-    static const cudaError_t attr =
+    const cudaError_t attr =
         cudaFuncSetAttribute(k_edge_features, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (attr != cudaSuccess) return (int)attr;
     if (d < 1 || d > kMaxDims) return (int)cudaErrorInvalidValue;
