@@ -66,3 +66,26 @@ def test_plan_create_without_gpu_fails_cleanly():
     prm = _native.frnn_plan_params(device=0, d_max=8, n_max=100, events_max=1, k_max_cap=8)
     assert lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)) == frnn.FRNN_ERR_CUDA
     assert not h.value
+
+
+def test_header_compiles_as_c99_and_links(tmp_path):
+    """include/frnn.h is a C header: a C99 program includes it (strict,
+    pedantic), links against libfrnn.so and calls an entry point that needs no
+    GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = frnn.library_path()
+    src = tmp_path / "use_frnn.c"
+    src.write_text('#include "frnn.h"\n'
+                   "int main(void) {\n"
+                   "    frnn_plan* p = 0;\n"
+                   "    return frnn_plan_test_stall_next_build(p) == FRNN_ERR_INVALID_ARG ? 0 : 1;\n"
+                   "}\n")
+    exe = tmp_path / "use_frnn"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                    str(src), lib, "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
+    assert subprocess.run([str(exe)]).returncode == 0
