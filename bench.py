@@ -52,9 +52,9 @@ L2_BYTES = 126 * 1024 * 1024
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 # warp instructions per query of the collect walk in the same ncu capture as
 # MEASURED_TRAFFIC (1.409 G instructions for 4.8 M queries)
-MEASURED_INSTR_PER_QUERY = 1_433_042_171 / 4_800_000
+MEASURED_INSTR_PER_QUERY = 1_433_034_302 / 4_800_000
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "a47fda4819ae", "bytes_per_point": 440_502_528 / 4_800_000}
+MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "ce730a6bfc50", "bytes_per_point": 440_871_424 / 4_800_000}
 
 
 def parse_args(argv=None):

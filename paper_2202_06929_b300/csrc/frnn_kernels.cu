@@ -48,11 +48,12 @@ constexpr int kSpinLimit = 1 << 22;                 // polls of one bounded wait
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and at most 1 s of it
 // kNN builds: cell edge as a fraction of the estimated k-th neighbour
 // distance.  Speed only (the ring walk's stop rule keeps any edge exact);
-// with the rings' gap pruning, 0.75 was within 0-28% of the fastest factor
-// over k = 4, 16, 64 on 120k-point 8-dim events and k = 16 on 1M-point
-// 12-dim events; 0.5 was up to 3x slower, and from 0.9 up the 12-dim events
-// grid fewer dims (a dim needs >= 4 cells) and ran 4x slower.
-constexpr float kKnnCellFactor = 0.75f;
+// with the rings' gap pruning, 0.8 was within 0-17% of the fastest factor
+// over k = 4, 16, 64 on 120k-point 8-dim events, k = 16 on 1M-point 12-dim
+// events and the 40k-140k-point events (0.75: up to 35%); 0.5 was up to 3x
+// slower, and from 0.9 up the 12-dim events grid fewer dims (a dim needs
+// >= 4 cells) and ran 4x slower.
+constexpr float kKnnCellFactor = 0.8f;
 // Margin (cells) on a gap between a query and a cell: each side's float32
 // cell coordinate is within 0.006 cells of (x - lo) / s.
 constexpr float kGapMargin = 1.0f / 64.0f;
