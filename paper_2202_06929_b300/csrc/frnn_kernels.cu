@@ -1443,125 +1443,125 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
     const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
     const unsigned group = nchunks >= 4 * nwarps ? (unsigned)kChunkGroup : 1u;
     for (;;) {
-    unsigned g0 = 0;
-    if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], group);
-    g0 = __shfl_sync(kFull, g0, 0);
-    if ((long long)g0 >= nchunks) break;
-    const long long gend = min((long long)g0 + group, nchunks);
-    for (long long ch = g0; ch < gend; ++ch) {
-        const long long q0 = ch << 5;
-        const long long q = q0 + lane;
-        const bool valid = q < P;
-        lane_event(st.ev, B, valid ? q : P - 1, le);
-        const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
-        int nvalid;
-        unsigned seg = stage_chunk<DP4>(xs4, q, valid, cs, le.b, sq, lane, &nvalid);
-        int deg = 0;
-        while (seg) {
-            const int a = __ffs(seg) - 1;
-            seg &= seg - 1;
-            const int e = seg ? __ffs(seg) - 1 : nvalid;
-            const int sb = __shfl_sync(kFull, le.b, a);
-            if (sb != plan_b) {
-                load_plan(ww, st.plan, sb, lane);
-                plan_b = sb;
-            }
-            if (ww.pl.skip) continue;
-            segment_cell(ww, sq + (a >> 1) * (2 * DP), a & 1, lane);
-            const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
-            for_each_run_group(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, [&](const Runs& rn) {
-            for (int base = 0; base < rn.total; base += 32) {
-                const int cand = candidate_at(rn, base + lane);
-                CandPk<DP4> cp;
-                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
-                const bool cv = cand >= 0;
-                // Every query meets itself exactly once (d2 = 0): it is counted
-                // here and taken out below, which keeps a self test out of this loop.
-#pragma unroll 2
-                for (int pp = p0; pp < p1; ++pp) {
-                    const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
-                    const int i0 = 2 * pp, i1 = 2 * pp + 1;
-                    const bool h0 = cv && (i0 >= a) && d.x <= r2;
-                    const bool h1 = cv && (i1 < e) && d.y <= r2;
-                    const unsigned m0 = __ballot_sync(kFull, h0);
-                    const unsigned m1 = __ballot_sync(kFull, h1);
-                    if (m0 | m1) {
-                        const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
-                        const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
-                        if (h0 && s0 < kRowSlots) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
-                        if (h1 && s1 < kRowSlots) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
-                        if (lane == i0) deg += __popc(m0);
-                        if (lane == i1) deg += __popc(m1);
-                    }
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], group);
+        g0 = __shfl_sync(kFull, g0, 0);
+        if ((long long)g0 >= nchunks) break;
+        const long long gend = min((long long)g0 + group, nchunks);
+        for (long long ch = g0; ch < gend; ++ch) {
+            const long long q0 = ch << 5;
+            const long long q = q0 + lane;
+            const bool valid = q < P;
+            lane_event(st.ev, B, valid ? q : P - 1, le);
+            const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
+            int nvalid;
+            unsigned seg = stage_chunk<DP4>(xs4, q, valid, cs, le.b, sq, lane, &nvalid);
+            int deg = 0;
+            while (seg) {
+                const int a = __ffs(seg) - 1;
+                seg &= seg - 1;
+                const int e = seg ? __ffs(seg) - 1 : nvalid;
+                const int sb = __shfl_sync(kFull, le.b, a);
+                if (sb != plan_b) {
+                    load_plan(ww, st.plan, sb, lane);
+                    plan_b = sb;
                 }
+                if (ww.pl.skip) continue;
+                segment_cell(ww, sq + (a >> 1) * (2 * DP), a & 1, lane);
+                const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
+                for_each_run_group(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, [&](const Runs& rn) {
+                    for (int base = 0; base < rn.total; base += 32) {
+                        const int cand = candidate_at(rn, base + lane);
+                        CandPk<DP4> cp;
+                        load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                        const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
+                        const bool cv = cand >= 0;
+                        // Every query meets itself exactly once (d2 = 0): it is counted
+                        // here and taken out below, which keeps a self test out of this loop.
+        #pragma unroll 2
+                        for (int pp = p0; pp < p1; ++pp) {
+                            const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
+                            const int i0 = 2 * pp, i1 = 2 * pp + 1;
+                            const bool h0 = cv && (i0 >= a) && d.x <= r2;
+                            const bool h1 = cv && (i1 < e) && d.y <= r2;
+                            const unsigned m0 = __ballot_sync(kFull, h0);
+                            const unsigned m1 = __ballot_sync(kFull, h1);
+                            if (m0 | m1) {
+                                const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
+                                const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
+                                if (h0 && s0 < kRowSlots) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
+                                if (h1 && s1 < kRowSlots) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
+                                if (lane == i0) deg += __popc(m0);
+                                if (lane == i1) deg += __popc(m1);
+                            }
+                        }
+                    }
+                });
             }
-            });
-        }
-        // pool space for the chunk's short rows
-        const int raw = deg;                 // includes the query itself
-        deg = raw > 0 ? raw - 1 : 0;         // |S_i|
-        const int cnt = min(deg, K);
-        const bool fast = valid && deg > 0 && deg <= kFast;
-        const int need = fast ? cnt : 0;
-        const int incl = warp_incl_scan(need, lane);
-        const int tot = __shfl_sync(kFull, incl, 31);
-        unsigned long long base_off = 0ull;
-        if (lane == 0 && tot > 0) base_off = atomicAdd(st.pool_ctr, (unsigned long long)tot);
-        base_off = __shfl_sync(kFull, base_off, 0);
-        const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
-        const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
-        const int self_j = valid ? __ldg(st.perm + q) : -1;
-        if (valid) {
-            st.pool_off[le.pt_off + self_j] = my_off;
-            st.cnt_o[le.pt_off + self_j] = cnt;
-        }
-        // rows that were not parked go on the emit walk's list
-        const bool longrow = valid && cnt > 0 && my_off < 0;
-        const unsigned lm = __ballot_sync(kFull, longrow);
-        if (lm) {
-            unsigned lbase = 0;
-            if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
-            lbase = __shfl_sync(kFull, lbase, 0);
-            if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
-        }
-        __syncwarp();
-        // The parked rows go to the pool sorted and cut at k: they fill
-        // [base_off, base_off + tot) in lane order.  The warp streams the
-        // rows' collected keys (the query's own key included) flat, each key
-        // finding its row by binary lifting over the lanes' prefix sums; a
-        // key's place in its row is the number of the row's keys below it,
-        // less one if the query's own key (d2 = 0, j = itself) is among them.
-        if (fits) {
-            const int nin = my_off >= 0 ? raw : 0;
-            const int incl_in = warp_incl_scan(nin, lane);
-            const int tot_in = __shfl_sync(kFull, incl_in, 31);
-            const int excl_in = incl_in - nin;
-            const int excl = incl - need;
-            for (int e0 = 0; e0 < tot_in; e0 += 32) {
-                const int e = e0 + lane;
-                const int L = find_run(incl_in, e);
-                const int xin = __shfl_sync(kFull, excl_in, L);
-                const int nl = __shfl_sync(kFull, nin, L);
-                const int ol = __shfl_sync(kFull, excl, L);
-                const int cl = __shfl_sync(kFull, cnt, L);
-                const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
-                if (e < tot_in) {
-                    const unsigned long long* row = keys + L * kRowStride;
-                    const unsigned long long kk = row[e - xin];
-                    if (kk != self_key) {
-                        int rank = (self_key < kk) ? -1 : 0;
-                        for (int y = 0; y < nl; ++y) rank += row[y] < kk;
-                        if (rank < cl) {
-                            st.pool[base_off + ol + rank] = (int)(unsigned)kk;
-                            if (emit) st.pool_d2[base_off + ol + rank] = __uint_as_float((unsigned)(kk >> 32));
+            // pool space for the chunk's short rows
+            const int raw = deg;                 // includes the query itself
+            deg = raw > 0 ? raw - 1 : 0;         // |S_i|
+            const int cnt = min(deg, K);
+            const bool fast = valid && deg > 0 && deg <= kFast;
+            const int need = fast ? cnt : 0;
+            const int incl = warp_incl_scan(need, lane);
+            const int tot = __shfl_sync(kFull, incl, 31);
+            unsigned long long base_off = 0ull;
+            if (lane == 0 && tot > 0) base_off = atomicAdd(st.pool_ctr, (unsigned long long)tot);
+            base_off = __shfl_sync(kFull, base_off, 0);
+            const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
+            const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
+            const int self_j = valid ? __ldg(st.perm + q) : -1;
+            if (valid) {
+                st.pool_off[le.pt_off + self_j] = my_off;
+                st.cnt_o[le.pt_off + self_j] = cnt;
+            }
+            // rows that were not parked go on the emit walk's list
+            const bool longrow = valid && cnt > 0 && my_off < 0;
+            const unsigned lm = __ballot_sync(kFull, longrow);
+            if (lm) {
+                unsigned lbase = 0;
+                if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
+                lbase = __shfl_sync(kFull, lbase, 0);
+                if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
+            }
+            __syncwarp();
+            // The parked rows go to the pool sorted and cut at k: they fill
+            // [base_off, base_off + tot) in lane order.  The warp streams the
+            // rows' collected keys (the query's own key included) flat, each key
+            // finding its row by binary lifting over the lanes' prefix sums; a
+            // key's place in its row is the number of the row's keys below it,
+            // less one if the query's own key (d2 = 0, j = itself) is among them.
+            if (fits) {
+                const int nin = my_off >= 0 ? raw : 0;
+                const int incl_in = warp_incl_scan(nin, lane);
+                const int tot_in = __shfl_sync(kFull, incl_in, 31);
+                const int excl_in = incl_in - nin;
+                const int excl = incl - need;
+                for (int e0 = 0; e0 < tot_in; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int L = find_run(incl_in, e);
+                    const int xin = __shfl_sync(kFull, excl_in, L);
+                    const int nl = __shfl_sync(kFull, nin, L);
+                    const int ol = __shfl_sync(kFull, excl, L);
+                    const int cl = __shfl_sync(kFull, cnt, L);
+                    const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
+                    if (e < tot_in) {
+                        const unsigned long long* row = keys + L * kRowStride;
+                        const unsigned long long kk = row[e - xin];
+                        if (kk != self_key) {
+                            int rank = (self_key < kk) ? -1 : 0;
+                            for (int y = 0; y < nl; ++y) rank += row[y] < kk;
+                            if (rank < cl) {
+                                st.pool[base_off + ol + rank] = (int)(unsigned)kk;
+                                if (emit) st.pool_d2[base_off + ol + rank] = __uint_as_float((unsigned)(kk >> 32));
+                            }
                         }
                     }
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
-    }
     }
 }
 
@@ -1675,69 +1675,69 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
                 // no cap: whole rows, written in candidate order
                 int nw0 = 0, nw1 = 0;
                 for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
-                for (int base = 0; base < rn.total; base += 32) {
-                    const int cand = candidate_at(rn, base + lane);
-                    CandPk<DP4> cp;
-                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                    const float2 d = dist2_pair<DP4>(sqp, cp);
-                    const bool t0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
-                    const bool t1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
-                    const unsigned m0 = __ballot_sync(kFull, t0);
-                    const unsigned m1 = __ballot_sync(kFull, t1);
-                    if (m0 | m1) {
-                        const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
-                        const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
-                        if (t0 && s0 < cnt0) {
-                            st.col[rs0 + s0] = j;
-                            if (emit) st.d2[rs0 + s0] = d.x;
+                    for (int base = 0; base < rn.total; base += 32) {
+                        const int cand = candidate_at(rn, base + lane);
+                        CandPk<DP4> cp;
+                        load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                        const float2 d = dist2_pair<DP4>(sqp, cp);
+                        const bool t0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                        const bool t1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                        const unsigned m0 = __ballot_sync(kFull, t0);
+                        const unsigned m1 = __ballot_sync(kFull, t1);
+                        if (m0 | m1) {
+                            const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                            const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
+                            if (t0 && s0 < cnt0) {
+                                st.col[rs0 + s0] = j;
+                                if (emit) st.d2[rs0 + s0] = d.x;
+                            }
+                            if (t1 && s1 < cnt1) {
+                                st.col[rs1 + s1] = j;
+                                if (emit) st.d2[rs1 + s1] = d.y;
+                            }
+                            nw0 += __popc(m0);
+                            nw1 += __popc(m1);
                         }
-                        if (t1 && s1 < cnt1) {
-                            st.col[rs1 + s1] = j;
-                            if (emit) st.d2[rs1 + s1] = d.y;
-                        }
-                        nw0 += __popc(m0);
-                        nw1 += __popc(m1);
                     }
-                }
                 });
                 continue;
             }
             unsigned long long thr0 = ~0ull, thr1 = ~0ull;
             int nk0 = 0, nk1 = 0;
             for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
-            for (int base = 0; base < rn.total; base += 32) {
-                const int cand = candidate_at(rn, base + lane);
-                CandPk<DP4> cp;
-                load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                const float2 d = dist2_pair<DP4>(sqp, cp);
-                const bool h0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
-                const bool h1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
-                if (!__any_sync(kFull, h0 || h1)) continue;
-                const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
-                const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
-                bool t0 = h0 && k0 < thr0, t1 = h1 && k1 < thr1;
-                unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
-                if (nk0 + 32 > cap && m0) {
-                    // only reached when |S_i| > k: keep the k smallest so far
-                    warp_sort_smem(keys0, nk0, lane);
-                    nk0 = K;
-                    thr0 = keys0[K - 1];
-                    t0 = t0 && k0 < thr0;
-                    m0 = __ballot_sync(kFull, t0);
+                for (int base = 0; base < rn.total; base += 32) {
+                    const int cand = candidate_at(rn, base + lane);
+                    CandPk<DP4> cp;
+                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                    const float2 d = dist2_pair<DP4>(sqp, cp);
+                    const bool h0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                    const bool h1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                    if (!__any_sync(kFull, h0 || h1)) continue;
+                    const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                    const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
+                    bool t0 = h0 && k0 < thr0, t1 = h1 && k1 < thr1;
+                    unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
+                    if (nk0 + 32 > cap && m0) {
+                        // only reached when |S_i| > k: keep the k smallest so far
+                        warp_sort_smem(keys0, nk0, lane);
+                        nk0 = K;
+                        thr0 = keys0[K - 1];
+                        t0 = t0 && k0 < thr0;
+                        m0 = __ballot_sync(kFull, t0);
+                    }
+                    if (nk1 + 32 > cap && m1) {
+                        warp_sort_smem(keys1, nk1, lane);
+                        nk1 = K;
+                        thr1 = keys1[K - 1];
+                        t1 = t1 && k1 < thr1;
+                        m1 = __ballot_sync(kFull, t1);
+                    }
+                    if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
+                    if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
+                    nk0 += __popc(m0);
+                    nk1 += __popc(m1);
+                    __syncwarp();
                 }
-                if (nk1 + 32 > cap && m1) {
-                    warp_sort_smem(keys1, nk1, lane);
-                    nk1 = K;
-                    thr1 = keys1[K - 1];
-                    t1 = t1 && k1 < thr1;
-                    m1 = __ballot_sync(kFull, t1);
-                }
-                if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
-                if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
-                nk0 += __popc(m0);
-                nk1 += __popc(m1);
-                __syncwarp();
-            }
             });
             if (on0) emit_row_out(st, keys0, nk0, rs0, cnt0, emit, lane);
             if (on1) emit_row_out(st, keys1, nk1, rs1, cnt1, emit, lane);
@@ -1758,7 +1758,8 @@ __global__ void __launch_bounds__(kPtThreads) k_knn_rows(DevState st)
     const int K = st.hdr->k;
     long long lo = 1, hi = 0, off = 0;
     int e0 = 0, kb = 0;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
         if (p < lo || p >= hi) {
             const int b = event_of_point(st.ev, B, p);
             off = st.ev[b].pt_off;
@@ -1969,8 +1970,11 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
                     // a slot whose points all lie farther than every open
                     // row's k_b-th key holds none of their neighbours
                     float prune = 0.f;
-                    if (!done0) prune = nk0 >= kb ? __uint_as_float((unsigned)(thr0 >> 32)) : __int_as_float(0x7f800000);
-                    if (!done1) prune = fmaxf(prune, nk1 >= kb ? __uint_as_float((unsigned)(thr1 >> 32)) : __int_as_float(0x7f800000));
+                    if (!done0)
+                        prune = nk0 >= kb ? __uint_as_float((unsigned)(thr0 >> 32)) : __int_as_float(0x7f800000);
+                    if (!done1)
+                        prune = fmaxf(prune, nk1 >= kb ? __uint_as_float((unsigned)(thr1 >> 32))
+                                                       : __int_as_float(0x7f800000));
                     for_each_ring_group(ww, rho, st.cell_start, lane, s_amin[wib], s_amax[wib], prune, s_box[wib][0],
                                         s_box[wib][1], batch);
                 }
@@ -2007,7 +2011,8 @@ inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
 template <int DP4>
 int collect_smem()
 {
-    return (kWalkThreads / 32) * (32 * 4 * DP4 * (int)sizeof(float) + 32 * kRowStride * (int)sizeof(unsigned long long));
+    return (kWalkThreads / 32) *
+           (32 * 4 * DP4 * (int)sizeof(float) + 32 * kRowStride * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>
