@@ -46,15 +46,15 @@ N_PER_EVENT, D, R, K = 120_000, 8, 0.1, 256
 KERNELS_PER_BUILD = 7
 STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "scan_rows", "walk_emit")
 L2_BYTES = 126 * 1024 * 1024
-# DRAM read + write bytes per point of the collect walk, from the ncu capture
-# summarised in profiles/walk_kernels_c2_batched40.md; valid only for the
-# kernel source it was taken on (traffic scales with the points processed).
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
-# warp instructions per query of the collect walk in the same ncu capture as
-# MEASURED_TRAFFIC (1.409 G instructions for 4.8 M queries)
-MEASURED_INSTR_PER_QUERY = 1_433_034_302 / 4_800_000
 KNN_K = 16       # k of the exact-kNN measurement
-MEASURED_TRAFFIC = {"workload": "c2", "stage": "walk_collect", "source_sha1_prefix": "ce730a6bfc50", "bytes_per_point": 440_871_424 / 4_800_000}
+AUTOTUNE_SPACE = "g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each"
+# DRAM read + write bytes per point and warp instructions per query of the
+# collect walk, from one ncu capture of the N=120k workload (40 events, 4.8 M
+# points); valid only for the kernel code it was taken on (the sha1 of the
+# kernel file without comments) and the walk form it ran.
+MEASURED_COLLECT = {"workload": "c2", "stage": "walk_collect", "walk": 1, "source_sha1_prefix": "ce730a6bfc50",
+                    "bytes_per_point": 440_871_424 / 4_800_000, "instr_per_query": 1_433_034_302 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -67,6 +67,8 @@ def parse_args(argv=None):
                          "c5/c5b: N=1M, D=12, r=0.15, K=128 (c5b: the cap binds)")
     ap.add_argument("--events", type=int, default=None, help="events per batched step (64; 8 for c5/c5b)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--walk", choices=["tuned", "auto", "candidates", "queries"], default="tuned",
+                    help="form of the neighbour walk: the autotuner's choice (tuned), or forced")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-queries", type=int, default=40_000,
                     help="queries of the CPU oracle sample (bounded CPU work)")
@@ -272,6 +274,13 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
+def walk_form(walk: int, d: int) -> int:
+    """The collect walk a build runs (the rule of frnn_tuning.walk): the
+    query-major form (2) for d <= 12 unless the candidate-major form (1) is
+    asked for; candidate-major above."""
+    return 1 if ((d + 3) // 4 > 3 or walk == 1) else 2
+
+
 def kernel_source_sha1() -> str:
     """sha1 of the kernel source with // comments removed and whitespace runs
     collapsed: a capture stays valid across comment edits, not code edits."""
@@ -282,18 +291,18 @@ def kernel_source_sha1() -> str:
     return hashlib.sha1(src.encode()).hexdigest()
 
 
-def measured_traffic(stage: str, n_total: int, workload: str = "c2"):
-    """roofline.traffic of the given stage on the captured workload (C2), or
-    None for another workload or once the kernel code changed."""
-    if workload != MEASURED_TRAFFIC["workload"]:
+def measured_collect(stage: str, workload: str, walk: int):
+    """The captured figures of the collect walk (MEASURED_COLLECT) when they
+    describe this launch: same stage, workload, walk form and kernel code;
+    else None."""
+    m = MEASURED_COLLECT
+    if workload != m["workload"] or stage != m["stage"] or walk != m["walk"]:
         return None
     try:
         sha = kernel_source_sha1()
     except OSError:
         return None
-    if stage != MEASURED_TRAFFIC["stage"] or not sha.startswith(MEASURED_TRAFFIC["source_sha1_prefix"]):
-        return None
-    return MEASURED_TRAFFIC["bytes_per_point"] * n_total
+    return m if sha.startswith(m["source_sha1_prefix"]) else None
 
 
 def stage_bytes(n_total: int, n_edges: int, d: int):
@@ -399,6 +408,17 @@ def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point:
 
 # --------------------------------------------------------------------------- CPU oracle
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_cpu_baseline(x, queries: int, seed: int = 0, r: float = R, k: int = K):
     import oracle
     n = x.shape[0]
@@ -406,7 +426,8 @@ def run_cpu_baseline(x, queries: int, seed: int = 0, r: float = R, k: int = K):
     t0 = time.perf_counter()
     oracle.radius_graph(x, r, k, queries=q)
     dt = time.perf_counter() - t0
-    return {"value": (len(q) / n) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": (len(q) / n) / dt, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"{len(q)} random query rows of one N={n} event (brute force over all {n} points), "
                       f"{dt:.2f} s; events/s = (rows / N) / s"}
 
@@ -466,11 +487,27 @@ def reference_arm(args, rank, world):
 
 # --------------------------------------------------------------------------- served
 
+def _trace_loads(srv, x_all, start, sizes, req, traces, warm, n_requests):
+    out = []
+    for f, rate, arr in traces:
+        res = srv.run_trace(x_all, start[req], sizes[req], arr)
+        lat = res["latency_s"][warm:] * 1e3
+        span = arr[-1] - arr[warm] if req.size > warm + 1 else res["wall_s"]
+        done_eps = n_requests / max(res["wall_s"] - arr[warm], 1e-9)
+        out.append({"offered_x_capacity": f, "offered_events_per_s": rate,
+                    "achieved_events_per_s": done_eps, "latency_ms_p50": percentile(lat, 50),
+                    "latency_ms_p99": percentile(lat, 99), "arrival_span_s": span})
+    return out
+
+
 def run_served(frnn, torch, n_requests: int, pool_events: int = 48, seed: int = 7):
     """Served workload: events of N ~ U[20k, 200k] (the N=120k generator),
-    D=8, r=0.1, K=256, Poisson arrivals at 0.25x..1.5x of the measured
-    capacity, continuous batching on 3 slots within a 40 GB device budget.
-    Requests draw from a pool of distinct events (seeded)."""
+    D=8, r=0.1, K=256, Poisson arrivals at 0.25x..1.5x of the continuous
+    batching server's measured capacity, host arrival to host rows.  The same
+    arrival traces go through two servers within a 40 GB device budget:
+    continuous batching (3 slots, up to 64 events per launch) and the plain
+    form (1 slot, one event per launch).  Requests draw from a pool of
+    distinct events (seeded)."""
     evs = [synth.make_event("c4", e) for e in range(pool_events)]
     sizes = np.array([e.shape[0] for e in evs], dtype=np.int64)
     start = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
@@ -478,32 +515,35 @@ def run_served(frnn, torch, n_requests: int, pool_events: int = 48, seed: int = 
     rng = np.random.default_rng(seed)
     warm = 200
     req = rng.integers(0, pool_events, size=warm + n_requests)
-    srv = frnn.Server(d=D, r=R, k=K, batch_points=2_000_000, batch_events=64, slots=3, edges_per_point=32,
-                      mem_budget_bytes=40 << 30)
-    try:
-        # capacity: every request present at t = 0
-        sat = srv.run_trace(x_all, start[req], sizes[req], np.zeros(req.size))
-        capacity = req.size / sat["wall_s"]
-        loads = []
-        for f in (0.25, 0.5, 1.0, 1.5):
-            rate = f * capacity
-            arr = np.cumsum(rng.exponential(1.0 / rate, size=req.size))
-            arr -= arr[0]
-            res = srv.run_trace(x_all, start[req], sizes[req], arr)
-            lat = res["latency_s"][warm:] * 1e3
-            span = arr[-1] - arr[warm] if req.size > warm + 1 else res["wall_s"]
-            done_eps = n_requests / max(res["wall_s"] - arr[warm], 1e-9)
-            loads.append({"offered_x_capacity": f, "offered_events_per_s": rate,
-                          "achieved_events_per_s": done_eps, "latency_ms_p50": percentile(lat, 50),
-                          "latency_ms_p99": percentile(lat, 99), "arrival_span_s": span})
-        return {"workload": "c4: N ~ U[20000, 200000] per event, D=8, r=0.1, K=256, Poisson arrivals",
-                "requests_per_load": n_requests, "warmup_requests": warm, "event_pool": pool_events,
-                "slots": 3, "batch_points": 2_000_000, "mem_budget_gb": 40,
-                "reserved_gb": srv.reserved_bytes() / 1e9,
-                "capacity_events_per_s": capacity, "loads": loads,
-                "latency_note": "arrival (host clock) to the event's CSR on the host"}
-    finally:
-        srv.close()
+    forms = {"batching": dict(batch_points=2_000_000, batch_events=64, slots=3),
+             "plain": dict(batch_points=int(sizes.max()), batch_events=1, slots=1)}
+    out = {"workload": "c4: N ~ U[20000, 200000] per event, D=8, r=0.1, K=256, Poisson arrivals",
+           "requests_per_load": n_requests, "warmup_requests": warm, "event_pool": pool_events,
+           "mem_budget_gb": 40, "latency_note": "arrival (host clock) to the event's CSR on the host"}
+    traces = None
+    for name in ("batching", "plain"):
+        srv = frnn.Server(d=D, r=R, k=K, edges_per_point=32, mem_budget_bytes=40 << 30, **forms[name])
+        try:
+            # capacity: every request present at t = 0
+            sat = srv.run_trace(x_all, start[req], sizes[req], np.zeros(req.size))
+            capacity = req.size / sat["wall_s"]
+            if traces is None:  # offered loads are fractions of the batching server's capacity
+                traces = []
+                for f in (0.25, 0.5, 1.0, 1.5):
+                    rate = f * capacity
+                    arr = np.cumsum(rng.exponential(1.0 / rate, size=req.size))
+                    traces.append((f, rate, arr - arr[0]))
+            loads = _trace_loads(srv, x_all, start, sizes, req, traces, warm, n_requests)
+            out[name] = {**forms[name], "reserved_gb": srv.reserved_bytes() / 1e9,
+                         "capacity_events_per_s": capacity, "loads": loads, "stats": srv.stats()}
+        finally:
+            srv.close()
+    out["p99_winner_per_load"] = [
+        {"offered_x_capacity": b["offered_x_capacity"],
+         "winner": "batching" if b["latency_ms_p99"] <= p["latency_ms_p99"] else "plain",
+         "p99_ms": {"batching": b["latency_ms_p99"], "plain": p["latency_ms_p99"]}}
+        for b, p in zip(out["batching"]["loads"], out["plain"]["loads"])]
+    return out
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -543,11 +583,16 @@ def main(argv=None):
         with torch.cuda.stream(stream):
             g, scale, ms = plan.autotune(x_dev, off, r, k, stream=stream)
             g1, scale1, ms1 = plan_one.autotune(x_dev[int(off[0]):int(off[1])], off[:2], r, k, stream=stream)
-        tuned = {"batched": {"g_max": g, "cell_scale": scale, "build_ms": ms},
-                 "plain": {"g_max": g1, "cell_scale": scale1, "build_ms": ms1},
+        tuned = {"batched": {"g_max": g, "cell_scale": scale, "walk": plan.get_tuning()[2], "build_ms": ms},
+                 "plain": {"g_max": g1, "cell_scale": scale1, "walk": plan_one.get_tuning()[2], "build_ms": ms1},
                  "seconds": time.perf_counter() - t0,
-                 "searched": "g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each",
-                 "cells_per_point": cpp}
+                 "searched": AUTOTUNE_SPACE, "cells_per_point": cpp}
+    if args.walk != "tuned":
+        w = {"auto": 0, "candidates": 1, "queries": 2}[args.walk]
+        for pl in (plan, plan_one):
+            g_, s_, _ = pl.get_tuning()
+            pl.set_tuning(g_, s_, w)
+    walk_used = walk_form(plan.get_tuning()[2], d)
 
     # ---- batched: the timed step
     with torch.cuda.stream(stream), ClockSampler(local) as clk:
@@ -578,27 +623,31 @@ def main(argv=None):
     events_all = sum_over_ranks(pg, float(B * args.steps), dev)
     value = events_all / (total_ms_max / 1e3)
 
-    # ---- plain: one event per call, cycling through the batch's events (the
-    # batch is 2x larger than L2, so each event's input is cold when reused)
+    # ---- plain: one event per call plus a stream sync, timed per event with
+    # CUDA events (device latency) and the host clock (call to sync), cycling
+    # through the batch's events (the batch is 2x larger than L2, so each
+    # event's input is cold when reused)
     plain_ms = []
+    plain_host_ms = []
     with torch.cuda.stream(stream):
         for e in range(min(B, 4)):
             lo, hi = int(off[e]), int(off[e + 1])
             plan_one.build(x_dev[lo:hi], r, k, stream=stream)
-        pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * B)]
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         for e in range(B):
             lo, hi = int(off[e]), int(off[e + 1])
-            pe[2 * e].record(stream)
+            t0 = time.perf_counter()
+            pe0.record(stream)
             plan_one.build(x_dev[lo:hi], r, k, stream=stream)
-            pe[2 * e + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        plain_ms = [pe[2 * e].elapsed_time(pe[2 * e + 1]) for e in range(B)]
-        plain_wall = pe[0].elapsed_time(pe[-1])
+            pe1.record(stream)
+            pe1.synchronize()
+            plain_host_ms.append(1e3 * (time.perf_counter() - t0))
+            plain_ms.append(pe0.elapsed_time(pe1))
     st = plan_one.last_status(stream)
     if st != 0:
         raise RuntimeError(f"plain status: {frnn.status_string(st)}")
-    plain_value = B / (plain_wall / 1e3)
+    plain_value = B / (sum(plain_host_ms) / 1e3)
 
     # ---- track labeling (connected components of the built graph, every edge kept)
     labeling = None
@@ -616,9 +665,14 @@ def main(argv=None):
             lab_ms.append(le0.elapsed_time(le1))
     if plan.last_status(stream) == 0:
         n_tracks = int((lab.cpu().numpy() == np.arange(n_total) - np.repeat(off[:-1], np.diff(off))).sum())
+        lab_bytes = 4 * (n_total + 1) + 4 * n_edges + 4 * n_total  # row offsets and columns read, labels written
+        lab_gbs = lab_bytes / (float(np.median(lab_ms)) / 1e3) / 1e9
         labeling = {"ms_per_step": float(np.median(lab_ms)), "components_per_step": n_tracks,
+                    "algorithmic_bytes": lab_bytes, "achieved_gbs": lab_gbs,
+                    "frac_of_hbm": lab_gbs / measured_peaks()[0],
                     "note": "frnn_label_components: weakly connected components of the step's graphs "
-                            "(all edges kept), 4 kernels, after the build on the same stream"}
+                            "(all edges kept), 4 kernels, after the build on the same stream; bytes: row "
+                            "offsets and columns read once, labels written once"}
 
     # ---- edge features for the filter stage: [x_i, x_j, d2] per edge of the same
     # graph, in 800k-edge batches (the filter network's batch, Sec. 3); outputs
@@ -641,9 +695,14 @@ def main(argv=None):
                 knn_ms.append(ke0.elapsed_time(ke1))
         if plan.last_status(stream) == 0:
             kms = float(np.median(knn_ms))
+            knn_bytes = 4 * n_total * d + 4 * (n_total + 1) + 4 * n_total * knn_k
+            knn_gbs = knn_bytes / (kms / 1e3) / 1e9
             knn = {"k": knn_k, "ms_per_step": kms, "events_per_s": B / (kms / 1e3),
+                   "algorithmic_bytes": knn_bytes, "achieved_gbs": knn_gbs,
+                   "frac_of_hbm": knn_gbs / measured_peaks()[0],
                    "note": "frnn_knn_graph_batched: the k nearest of every point (no radius) over the step's "
-                           "events, device time per step, median of 5 after one warm-up"}
+                           "events, device time per step, median of 5 after one warm-up; bytes: points read "
+                           "once, CSR written once"}
 
     # ---- per-stage times of the batched build (CUDA events between stages)
     stage_ms = {s: [] for s in STAGES}
@@ -656,8 +715,15 @@ def main(argv=None):
     dom = max(stage_avg, key=stage_avg.get)
     sbytes = stage_bytes(n_total, n_edges, d)
     hbm_peak, peak_kind = measured_peaks()
-    achieved = sbytes[dom] / (stage_avg[dom] / 1e3) / 1e9
+    # the build's algorithmic bytes (read the points once, write the CSR once)
     whole_bytes = 4 * n_total * d + 4 * (n_total + 1) + 4 * n_edges
+    achieved = whole_bytes / (stage_avg[dom] / 1e3) / 1e9
+    stages = {}
+    for sname in STAGES:
+        ms_ = stage_avg[sname]
+        gbs = sbytes[sname] / (ms_ / 1e3) / 1e9 if ms_ > 0 else None
+        stages[sname] = {"ms": ms_, "algorithmic_bytes": sbytes[sname], "achieved_gbs": gbs,
+                         "frac": gbs / hbm_peak if gbs is not None else None}
 
     # ---- e2e: host buffers in, host CSR out.  Main figure: the server's trace
     # call (frnn_server_run_trace) with every event of K steps present at t = 0:
@@ -725,7 +791,7 @@ def main(argv=None):
     alu = None
     issue = None
     if rank == 0:
-        g_used, s_used = plan.get_tuning()
+        g_used, s_used, _ = plan.get_tuning()
         mean_cand, g_grid = host_candidates(x_host[off[0]:off[1]], r, g_used, s_used, cpp)
         row_len = np.diff(plan.build_batched(x_dev, off, r, k, stream=stream).to_host()["row_ptr"].astype(np.int64))
         torch.cuda.synchronize(dev)
@@ -735,9 +801,9 @@ def main(argv=None):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_tops = n_sm * 128 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks["sm_max_mhz"] else None
         achieved_tops = ops / (total_ms_max / args.steps / 1e3) / 1e12
-        if (dom == MEASURED_TRAFFIC["stage"] and measured_traffic(dom, n_total, args.workload) is not None
-                and clocks["sm_max_mhz"]):
-            instr = MEASURED_INSTR_PER_QUERY * n_total
+        cap = measured_collect(dom, args.workload, walk_used)
+        if cap is not None and clocks["sm_max_mhz"]:
+            instr = cap["instr_per_query"] * n_total
             peak_g = 4 * n_sm * clocks["sm_max_mhz"] * 1e6 / 1e9
             ach_g = instr / (stage_avg[dom] / 1e3) / 1e9
             issue = {"warp_instructions_per_launch": instr, "achieved_g_per_s": ach_g, "peak_g_per_s": peak_g,
@@ -774,14 +840,25 @@ def main(argv=None):
                         "event_latency_note": "every event of a batch completes with its step"},
             "plain": {"events_per_s": plain_value, "latency_ms_p50": percentile(plain_ms, 50),
                       "latency_ms_p99": percentile(plain_ms, 99),
-                      "note": "one event per call (CUDA graph replay per event), device time per event"},
+                      "host_ms_p50": percentile(plain_host_ms, 50), "host_ms_p99": percentile(plain_host_ms, 99),
+                      "note": "one event per call (CUDA graph replay per event) plus a stream sync; latency = "
+                              "device time per event (CUDA events), host_ms = call to sync; events/s from the host "
+                              "times"},
             "batched_over_plain": value / plain_value / world,
+            "walk": {1: "candidate-major", 2: "query-major"}[walk_used],
             "stages_ms": stage_avg,
+            "stages": stages,
             "roofline": {"bound": "hbm", "kernel": "k_" + dom,
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": measured_traffic(dom, n_total, args.workload), "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": sbytes[dom],
+                         "traffic": (cap["bytes_per_point"] * n_total
+                                     if (cap := measured_collect(dom, args.workload, walk_used)) else None),
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": whole_bytes,
+                         "algorithmic_bytes_note": "4 N D + 4 (N + 1) + 4 E: the points read once and the CSR "
+                                                   "written once, over the dominant kernel's CUDA-event time",
                          "launch_ms": stage_avg[dom],
+                         "stage_bytes_view": {"bytes": sbytes[dom], "frac": stages[dom]["frac"],
+                                              "note": "the kernel's own unavoidable reads and writes"},
                          "whole_build": {"algorithmic_bytes": whole_bytes,
                                          "achieved_gbs": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9,
                                          "frac": whole_bytes / (total_ms_max / args.steps / 1e3) / 1e9 / hbm_peak},

@@ -100,15 +100,29 @@ typedef struct {
 } frnn_csr;
 
 /*
- * Cell-grid tuning (speed only; the result never depends on it).
+ * Cell-grid and walk tuning (speed only; the result never depends on it).
  * g_max: most gridded dimensions, 1..6 (0 = 4); a cell has 3^(g-1) runs of
  * neighbouring cells, and a dimension is only gridded while the event's cell
  * table (cells_per_point x n + 4096 slots) has room.  cell_scale: cell edge /
  * r, >= 1 (0 = 1).  The dimensions gridded are always the ones of widest extent.
+ * walk: how the neighbour walk maps work to the 32 lanes of a warp:
+ *   FRNN_WALK_AUTO (0)       query-major where it exists (d <= 12), else
+ *                            candidate-major;
+ *   FRNN_WALK_CANDIDATES (1) the lanes hold 32 candidates of a cell's
+ *                            neighbourhood at a time, tested against the
+ *                            cell's queries two per packed operation;
+ *   FRNN_WALK_QUERIES (2)    a lane per query, each streaming the candidates
+ *                            of its own cell's neighbourhood (d <= 12; larger
+ *                            d falls back to FRNN_WALK_CANDIDATES).
  */
+#define FRNN_WALK_AUTO 0
+#define FRNN_WALK_CANDIDATES 1
+#define FRNN_WALK_QUERIES 2
+
 typedef struct {
     int g_max;
     float cell_scale;
+    int walk;
 } frnn_tuning;
 
 /*
@@ -304,8 +318,10 @@ FRNN_API int frnn_plan_test_stall_next_build(frnn_plan* plan);
  *                col_capacity) or FRNN_ERR_TIMEOUT.
  *   stream       cudaStream_t; asynchronous, no host synchronisation.
  * Runs on the calling thread's current device.  The first call on a device
- * looks up the array's device address and the launch shapes; make that first
- * call before any stream capture.  All calls on a device share the array:
+ * (and the first with a new d rounded up to 4) looks up the array's device
+ * address and the launch shapes, which are not stream-ordered calls: make it
+ * before any stream capture.  Such a set-up call on a capturing stream
+ * returns FRNN_ERR_INVALID_ARG and enqueues nothing.  All calls on a device share the array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and must be serialised by the caller.  Each call clears what must
  * start at zero, so results never depend on an earlier call.
@@ -318,38 +334,68 @@ FRNN_API int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, float 
 /*
  * Serving: events arriving over time, built with continuous batching.
  * (The paper runs the pipeline per event inside a multithreaded C++ host,
- * Sec. 4, and names a model server as future work, Sec. 6.)  A server owns
- * `slots` plans, each with its own stream and its device memory reserved at
- * creation; a dispatcher thread starts a batched build on every free slot with
- * the requests that have arrived and not started, in arrival order, as many
- * as fit (batch_points points, batch_events events).  Batches on different
- * slots overlap on the device, and requests arriving meanwhile are admitted
- * as slots free up.  Each request's rows are identical to a separate
- * frnn_build_graph of the same points.
+ * Sec. 4, and names a model server as future work, Sec. 6.)  On each of its
+ * devices a server owns `slots` regular slots and one spill slot: a slot is a
+ * plan with its own stream, its device memory reserved at creation within the
+ * per-device budget.  A dispatcher thread starts a batched build on every free
+ * slot with the requests that have arrived and not started, in arrival order,
+ * as many as fit the slot: batch_points points, batch_events events, and the
+ * slot's edges (a request's edges are estimated from the edges per point of
+ * the requests finished so far until a build has counted them exactly).
+ * Batches on different slots overlap on the device, and requests arriving
+ * meanwhile are admitted as slots free up.  When slots on several devices are
+ * free, the device with the fewest points in flight is served first.
+ *
+ * Edge overflow is per request: a batch whose edges exceed its slot completes
+ * the requests whose edges fit and re-queues the others, at the front of the
+ * queue and with their exact edge counts, onto a regular slot if they fit one,
+ * else alone onto a spill slot (room for batch_points x k edges, or for as
+ * many edges as the budget leaves).  Only a request with more edges than the
+ * spill slot holds fails, with FRNN_ERR_OVERFLOW.  Each request's rows are
+ * identical to a separate frnn_build_graph of the same points.
  */
 typedef struct frnn_server frnn_server;
 
 typedef struct {
-    int device;
+    int device;                /* device of the slots when n_devices is 0             */
     int d;                     /* embedding dimension of every request, 1..64        */
     float r;                   /* radius (finite, > 0)                                */
     int k;                     /* neighbour cap, 1..1024                              */
     int64_t batch_points;      /* points of one batched launch (also the largest event) */
     int batch_events;          /* events of one batched launch                        */
-    int slots;                 /* batches in flight at once, 1..64                    */
-    int edges_per_point;       /* edge capacity of a slot per point (0 = min(32, k))  */
-    uint64_t mem_budget_bytes; /* device memory all slots may reserve (0 = no limit) */
+    int slots;                 /* regular slots per device, 1..64                     */
+    int edges_per_point;       /* edge capacity of a regular slot per point (0 = min(32, k)) */
+    uint64_t mem_budget_bytes; /* device memory the slots of one device may reserve (0 = no limit) */
+    int n_devices;             /* 0: the one device `device`; else devices[0 .. n_devices) */
+    const int* devices;        /* host array of device ordinals, read during create;
+                                  a device listed twice gets two independent sets of slots */
 } frnn_server_params;
+
+/* Counters of a server (frnn_server_get_stats). */
+typedef struct {
+    uint64_t batches;               /* batched builds finished                          */
+    uint64_t spill_batches;         /* ... of them on a spill slot                       */
+    uint64_t readmitted;            /* requests re-queued after their batch overflowed   */
+    uint64_t requests_done;         /* requests finished (any status)                    */
+    uint64_t max_queue;             /* most requests waiting at once                     */
+    uint64_t regular_edge_capacity; /* edges a regular slot holds                        */
+    uint64_t spill_edge_capacity;   /* edges a spill slot holds                          */
+} frnn_server_stats;
 
 /*
  * Create a server and its dispatcher thread.  Device memory of all slots is
- * reserved here: FRNN_ERR_OOM if it exceeds mem_budget_bytes (or the device).
- * Errors: INVALID_ARG, OOM, CUDA.
+ * reserved here: FRNN_ERR_OOM if one device's slots (the regular ones plus a
+ * spill slot at least as large) exceed mem_budget_bytes, or the device.
+ * Errors: INVALID_ARG (sizes out of range, batch_points * k >= 2^31, a bad
+ * device ordinal), OOM, CUDA.
  */
 FRNN_API int frnn_server_create(frnn_server** out, const frnn_server_params* p);
 
-/* Device bytes the server reserved for its slots. */
+/* Device bytes the server reserved for its slots (all devices). */
 FRNN_API int frnn_server_reserved_bytes(const frnn_server* srv, uint64_t* bytes);
+
+/* Copy the server's counters to *stats.  Errors: INVALID_ARG. */
+FRNN_API int frnn_server_get_stats(frnn_server* srv, frnn_server_stats* stats);
 
 /*
  * Queue one event (host float32 [n][d]; the buffer must stay valid and
@@ -360,11 +406,19 @@ FRNN_API int frnn_server_reserved_bytes(const frnn_server* srv, uint64_t* bytes)
 FRNN_API int frnn_server_submit(frnn_server* srv, const float* host_emb, int64_t n, uint64_t* ticket);
 
 /*
+ * Non-blocking check: *done = 1 once the event of `ticket` is finished (a
+ * following frnn_server_wait returns without waiting), else 0.  Errors:
+ * INVALID_ARG (NULL, or a ticket unknown or already waited for).
+ */
+FRNN_API int frnn_server_poll(frnn_server* srv, uint64_t ticket, int* done);
+
+/*
  * Block until the event of `ticket` is built, then copy its CSR (event-local
  * indices) to host buffers: row_ptr [n + 1], col [col_capacity].  *n_edges
  * and *latency_s (arrival to rows on the host) may be NULL.  Each ticket can
- * be waited for once.  Returns the event's status (OVERFLOW if col_capacity
- * is too small, or if the slot's edge capacity was exceeded).
+ * be waited for once.  Returns the event's status: OVERFLOW if col_capacity
+ * is too small, or if the event's edges exceed even a spill slot (*n_edges
+ * then receives the edge count).
  */
 FRNN_API int frnn_server_wait(frnn_server* srv, uint64_t ticket, int32_t* row_ptr, int32_t* col,
                               int64_t col_capacity, int64_t* n_edges, double* latency_s);

@@ -35,7 +35,7 @@ ABI_FUNCTIONS = (
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
     "frnn_label_components", "frnn_edge_features", "frnn_knn_graph_batched",
-    "frnn_plan_test_stall_next_build",
+    "frnn_plan_test_stall_next_build", "frnn_server_poll", "frnn_server_get_stats",
 )
 
 
@@ -53,13 +53,23 @@ class frnn_csr(ctypes.Structure):
 
 
 class frnn_tuning(ctypes.Structure):
-    _fields_ = [("g_max", ctypes.c_int), ("cell_scale", ctypes.c_float)]
+    _fields_ = [("g_max", ctypes.c_int), ("cell_scale", ctypes.c_float), ("walk", ctypes.c_int)]
+
+
+FRNN_WALK_AUTO, FRNN_WALK_CANDIDATES, FRNN_WALK_QUERIES = 0, 1, 2
 
 
 class frnn_server_params(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_float), ("k", ctypes.c_int),
                 ("batch_points", ctypes.c_int64), ("batch_events", ctypes.c_int), ("slots", ctypes.c_int),
-                ("edges_per_point", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64)]
+                ("edges_per_point", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
+                ("n_devices", ctypes.c_int), ("devices", ctypes.POINTER(ctypes.c_int))]
+
+
+class frnn_server_stats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("spill_batches", ctypes.c_uint64), ("readmitted", ctypes.c_uint64),
+                ("requests_done", ctypes.c_uint64), ("max_queue", ctypes.c_uint64),
+                ("regular_edge_capacity", ctypes.c_uint64), ("spill_edge_capacity", ctypes.c_uint64)]
 
 
 _lib = None
@@ -98,6 +108,8 @@ def load():
     lib.frnn_server_reserved_bytes.argtypes = [vp, P(ctypes.c_uint64)]
     lib.frnn_server_submit.argtypes = [vp, vp, i64, P(ctypes.c_uint64)]
     lib.frnn_server_wait.argtypes = [vp, ctypes.c_uint64, vp, vp, i64, P(ctypes.c_int64), P(ctypes.c_double)]
+    lib.frnn_server_poll.argtypes = [vp, ctypes.c_uint64, P(ctypes.c_int)]
+    lib.frnn_server_get_stats.argtypes = [vp, P(frnn_server_stats)]
     lib.frnn_server_run_trace.argtypes = [vp, vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_double), i32,
                                           P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double)]
     lib.frnn_server_destroy.argtypes = [vp]
@@ -257,14 +269,15 @@ class Plan:
     def handle(self) -> int:
         return int(self._h.value or 0)
 
-    def set_tuning(self, g_max: int = 0, cell_scale: float = 0.0) -> None:
-        t = frnn_tuning(g_max=g_max, cell_scale=cell_scale)
+    def set_tuning(self, g_max: int = 0, cell_scale: float = 0.0, walk: int = FRNN_WALK_AUTO) -> None:
+        t = frnn_tuning(g_max=g_max, cell_scale=cell_scale, walk=walk)
         _check(load().frnn_plan_set_tuning(self._h, ctypes.byref(t)), "frnn_plan_set_tuning")
 
-    def get_tuning(self) -> tuple[int, float]:
+    def get_tuning(self) -> tuple[int, float, int]:
+        """(g_max, cell_scale, walk) used by the next builds."""
         t = frnn_tuning()
         _check(load().frnn_plan_get_tuning(self._h, ctypes.byref(t)), "frnn_plan_get_tuning")
-        return int(t.g_max), float(t.cell_scale)
+        return int(t.g_max), float(t.cell_scale), int(t.walk)
 
     def autotune(self, emb, ev_off, r: float, k: int, stream=None) -> tuple[int, float, float]:
         """frnn_plan_autotune on this batch: returns (g_max, cell_scale, ms) of
@@ -404,14 +417,18 @@ def plan_bytes(n_max: int, d_max: int, k_max_cap: int, events_max: int = 1, edge
 
 class Server:
     """Continuous-batching graph server (frnn_server_*): submit host events,
-    wait for their CSR; batches run on `slots` concurrent streams."""
+    wait for their CSR; batches run on `slots` concurrent streams per device
+    (`devices`: a list of device ordinals, default [device])."""
 
     def __init__(self, d: int, r: float, k: int, batch_points: int, batch_events: int = 64, slots: int = 2,
-                 edges_per_point: int = 0, mem_budget_bytes: int = 0, device: int = 0):
+                 edges_per_point: int = 0, mem_budget_bytes: int = 0, device: int = 0, devices=None):
         lib = load()
+        devs = list(devices) if devices else []
+        arr = (ctypes.c_int * max(len(devs), 1))(*devs)
         prm = frnn_server_params(device=device, d=d, r=r, k=k, batch_points=batch_points,
                                  batch_events=batch_events, slots=slots, edges_per_point=edges_per_point,
-                                 mem_budget_bytes=mem_budget_bytes)
+                                 mem_budget_bytes=mem_budget_bytes, n_devices=len(devs),
+                                 devices=ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if devs else None)
         h = ctypes.c_void_p()
         _check(lib.frnn_server_create(ctypes.byref(h), ctypes.byref(prm)), "frnn_server_create")
         self._h = h
@@ -440,6 +457,17 @@ class Server:
         b = ctypes.c_uint64(0)
         _check(load().frnn_server_reserved_bytes(self._h, ctypes.byref(b)), "frnn_server_reserved_bytes")
         return int(b.value)
+
+    def stats(self) -> dict:
+        st = frnn_server_stats()
+        _check(load().frnn_server_get_stats(self._h, ctypes.byref(st)), "frnn_server_get_stats")
+        return {name: int(getattr(st, name)) for name, _ in frnn_server_stats._fields_}
+
+    def poll(self, ticket: int) -> bool:
+        """True once the event of `ticket` is done (wait() then returns at once)."""
+        done = ctypes.c_int(0)
+        _check(load().frnn_server_poll(self._h, ticket, ctypes.byref(done)), "frnn_server_poll")
+        return bool(done.value)
 
     def submit(self, x: np.ndarray) -> int:
         x = np.ascontiguousarray(x, dtype=np.float32)

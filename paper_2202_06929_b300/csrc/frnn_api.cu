@@ -43,6 +43,7 @@ int next_pow2(int v)
 struct GraphEntry {
     int dp4 = 0;
     int cap = 0;
+    int walk = 0;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -50,7 +51,7 @@ struct GraphEntry {
 
 struct frnn_plan {
     frnn_plan_params prm{};
-    frnn_tuning tuning{4, 1.0f};
+    frnn_tuning tuning{4, 1.0f, 0};
     int n_sm = 0;
     int dp_max = 0;
     long long cells_max = 0;
@@ -157,17 +158,18 @@ int launch(frnn_plan* p, int dp4, int cap, cudaStream_t s, cudaEvent_t* stage_ev
     LaunchCfg cfg;
     int rc = get_walk_cfg(p, dp4, cap, &cfg);
     if (rc != FRNN_OK) return rc;
+    const int walk = resolve_walk(p->tuning.walk, dp4);
     if (stage_ev || !(p->prm.flags & FRNN_USE_GRAPH))
-        return launch_build(p->st, dp4, cfg, s, stage_ev) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
+        return launch_build(p->st, dp4, cfg, walk, s, stage_ev) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
     GraphEntry* ge = nullptr;
     for (int i = 0; i < p->n_graphs; ++i)
-        if (p->graphs[i].dp4 == dp4 && p->graphs[i].cap == cap) ge = &p->graphs[i];
+        if (p->graphs[i].dp4 == dp4 && p->graphs[i].cap == cap && p->graphs[i].walk == walk) ge = &p->graphs[i];
     if (!ge) {
         if (p->n_graphs >= 32) return FRNN_ERR_CAPACITY;
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return FRNN_ERR_CUDA;
-        const int lrc = launch_build(p->st, dp4, cfg, p->cap_stream, nullptr);
+        const int lrc = launch_build(p->st, dp4, cfg, walk, p->cap_stream, nullptr);
         const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
         if (lrc != 0 || ce != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -184,6 +186,7 @@ int launch(frnn_plan* p, int dp4, int cap, cudaStream_t s, cudaEvent_t* stage_ev
         ge = &p->graphs[p->n_graphs++];
         ge->dp4 = dp4;
         ge->cap = cap;
+        ge->walk = walk;
         ge->exec = ex;
     }
     return cudaGraphLaunch(ge->exec, s) == cudaSuccess ? FRNN_OK : FRNN_ERR_CUDA;
@@ -467,8 +470,10 @@ int frnn_plan_set_tuning(frnn_plan* p, const frnn_tuning* t)
     const int g = t->g_max == 0 ? 4 : t->g_max;  // default 4; up to kMaxG when the cell budget allows
     const float cs = t->cell_scale == 0.f ? 1.0f : t->cell_scale;
     if (g < 1 || g > kMaxG || !(cs >= 1.0f) || !std::isfinite(cs) || cs > 1e6f) return FRNN_ERR_INVALID_ARG;
+    if (t->walk < kWalkAuto || t->walk > kWalkQueryMajor) return FRNN_ERR_INVALID_ARG;
     p->tuning.g_max = g;
     p->tuning.cell_scale = cs;
+    p->tuning.walk = t->walk;
     return FRNN_OK;
 }
 
@@ -706,28 +711,10 @@ int frnn_plan_test_stall_next_build(frnn_plan* p)
 
 int frnn_get_last_status(frnn_plan* p, void* stream)
 {
-    if (!p) return FRNN_ERR_INVALID_ARG;
-    DeviceGuard dg(p->prm.device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return FRNN_ERR_CUDA;
-    }
     unsigned word = 0;
-    if (cudaMemcpyAsync(&word, p->st.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemsetAsync(p->st.status, 0, sizeof(unsigned), s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return FRNN_ERR_CUDA;
-    }
-    if (word & kStTimeout) {
-        // a wait gave up part-way: restore the between-builds state; the last
-        // graph is not valid, so labeling and edge features refuse it
-        reset_device_state(p, s);
-        cudaStreamSynchronize(s);
-        p->has_last = false;
-        return FRNN_ERR_TIMEOUT;
-    }
+    const int rc = read_status_bits(p, stream, &word);
+    if (rc != FRNN_OK) return rc;
+    if (word & kStTimeout) return FRNN_ERR_TIMEOUT;
     if (word & kStOverflow) return FRNN_ERR_OVERFLOW;
     if (word & kStNonfinite) return FRNN_ERR_NONFINITE_INPUT;
     return FRNN_OK;
@@ -784,3 +771,31 @@ int frnn_build_graph_host(frnn_plan* p, const float* h_emb, const int64_t* ev_of
 }
 
 }  // extern "C"
+
+int frnn::read_status_bits(frnn_plan* p, void* stream, unsigned* bits)
+{
+    if (!p || !bits) return FRNN_ERR_INVALID_ARG;
+    *bits = 0;
+    DeviceGuard dg(p->prm.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    unsigned word = 0;
+    if (cudaMemcpyAsync(&word, p->st.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(p->st.status, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    if (word & kStTimeout) {
+        // a wait gave up part-way: restore the between-builds state; the last
+        // graph is not valid, so labeling and edge features refuse it
+        reset_device_state(p, s);
+        cudaStreamSynchronize(s);
+        p->has_last = false;
+    }
+    *bits = word;
+    return FRNN_OK;
+}

@@ -3,6 +3,8 @@
 
 #include <cstdint>
 
+struct frnn_plan;
+
 namespace frnn {
 
 constexpr int kMaxG = 6;            // most gridded dimensions (3^(g-1) runs per cell)
@@ -120,11 +122,26 @@ __device__ __forceinline__ bool timed_out(const DevState& st)
 }
 #endif
 
+// Forms of the collect walk (frnn_tuning.walk).
+constexpr int kWalkAuto = 0;
+constexpr int kWalkCandMajor = 1;   // lanes hold candidates; a segment's queries in packed pairs
+constexpr int kWalkQueryMajor = 2;  // a lane per query streams its segment's candidates (d <= 12)
+constexpr int kMaxDp4QueryMajor = 3;
+
+// The collect walk a build runs: the query-major form where it exists
+// (rows of up to 12 floats) unless the tuning asks for the other.
+inline int resolve_walk(int walk, int dp4)
+{
+    if (dp4 > kMaxDp4QueryMajor) return kWalkCandMajor;
+    return walk == kWalkCandMajor ? kWalkCandMajor : kWalkQueryMajor;
+}
+
 struct LaunchCfg {
     int grid_pt;       // per-point kernels (persistent: blocks loop over chunks)
     int grid_scatter;  // scatter: as many blocks as are resident at once
     int grid_scan;     // scans (persistent: blocks take tiles from a counter)
     int grid_count;    // count walk (persistent: warps stride over queries)
+    int grid_count_q;  // its query-major form
     int grid_fill;     // fill walk
     int fill_cap;      // per-warp key buffer of the fill walk (power of two, >= k + 32)
     int fill_smem;     // its dynamic shared memory in bytes
@@ -133,7 +150,8 @@ struct LaunchCfg {
 // Host-side launchers (frnn_kernels.cu).  All return a cudaError_t value.
 // stage_events: NULL, or kStages + 1 cudaEvent_t recorded around the stages.
 constexpr int kStages = 7;
-int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream, void* stage_events);
+// walk: kWalkCandMajor or kWalkQueryMajor (the latter for dp4 <= kMaxDp4QueryMajor only).
+int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, int walk, void* stream, void* stage_events);
 int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg);
 // Weakly connected components of the last build (frnn_label.cu); parent is
 // n_total ints of scratch, labels receives event-local component labels.
@@ -144,5 +162,11 @@ int launch_edge_features(const DevState& st, const float* emb, int d, long long 
 int config_pt(int n_sm, LaunchCfg* cfg);
 // The k-nearest-neighbour build (no radius): grid, fixed-length rows, ring walk.
 int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream);
+
+// Synchronise the stream, then return in *bits and clear the status bits the
+// plan's kernels latched (kStNonfinite, kStTimeout, kStOverflow); after a
+// timeout the plan's between-builds state is restored, as by
+// frnn_get_last_status (frnn_api.cu).  Returns FRNN_OK or an error status.
+int read_status_bits(struct ::frnn_plan* p, void* stream, unsigned* bits);
 
 }  // namespace frnn

@@ -1405,6 +1405,97 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
     return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
 }
 
+// End of a chunk of the collect walk.  Lane i holds query q = q0 + i and
+// raw = its hit count (the query itself included); keys[i * kRowStride ..]
+// holds its first min(raw, kRowSlots) keys in hit order.  Writes every
+// query's min(|S_i|, k) and pool slot, lists the rows that are not parked for
+// the emit walk, and parks the short rows in the pool sorted and cut at k.
+// BY_POS: the keys' low words hold the candidate's sorted position (the
+// query-major walk), replaced here by its event-local index before ranking.
+template <bool BY_POS>
+__device__ __forceinline__ void park_rows(const DevState& st, unsigned long long* keys, int raw, bool valid,
+                                          long long q, const LaneEvent& le, int lane)
+{
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int K = st.hdr->k;
+    const int emit = st.hdr->emit_d2;
+    const long long pool_cap = st.hdr->edge_capacity;
+    // pool space for the chunk's short rows
+    const int deg = raw > 0 ? raw - 1 : 0;  // |S_i|
+    const int cnt = min(deg, K);
+    const bool fast = valid && deg > 0 && deg <= kFast;
+    const int need = fast ? cnt : 0;
+    const int incl = warp_incl_scan(need, lane);
+    const int tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long base_off = 0ull;
+    if (lane == 0 && tot > 0) base_off = atomicAdd(st.pool_ctr, (unsigned long long)tot);
+    base_off = __shfl_sync(kFull, base_off, 0);
+    const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
+    const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
+    const int self_j = valid ? __ldg(st.perm + q) : -1;
+    if (valid) {
+        st.pool_off[le.pt_off + self_j] = my_off;
+        st.cnt_o[le.pt_off + self_j] = cnt;
+    }
+    // rows that were not parked go on the emit walk's list
+    const bool longrow = valid && cnt > 0 && my_off < 0;
+    const unsigned lm = __ballot_sync(kFull, longrow);
+    if (lm) {
+        unsigned lbase = 0;
+        if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
+        lbase = __shfl_sync(kFull, lbase, 0);
+        if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
+    }
+    if (BY_POS && my_off >= 0) {
+        // sorted position -> event-local index (loads issued four at a time)
+        unsigned long long* row = keys + lane * kRowStride;
+        for (int y = 0; y < raw; y += 4) {
+            int jj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) jj[u] = (y + u < raw) ? __ldg(st.perm + (unsigned)row[y + u]) : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (y + u < raw) row[y + u] = (row[y + u] & 0xffffffff00000000ull) | (unsigned)jj[u];
+        }
+    }
+    __syncwarp();
+    // The parked rows go to the pool sorted and cut at k: they fill
+    // [base_off, base_off + tot) in lane order.  The warp streams the rows'
+    // collected keys (the query's own key included) flat, each key finding its
+    // row by binary lifting over the lanes' prefix sums; a key's place in its
+    // row is the number of the row's keys below it, less one if the query's
+    // own key (d2 = 0, j = itself) is among them.
+    if (fits) {
+        const int nin = my_off >= 0 ? raw : 0;
+        const int incl_in = warp_incl_scan(nin, lane);
+        const int tot_in = __shfl_sync(kFull, incl_in, 31);
+        const int excl_in = incl_in - nin;
+        const int excl = incl - need;
+        for (int e0 = 0; e0 < tot_in; e0 += 32) {
+            const int e = e0 + lane;
+            const int L = find_run(incl_in, e);
+            const int xin = __shfl_sync(kFull, excl_in, L);
+            const int nl = __shfl_sync(kFull, nin, L);
+            const int ol = __shfl_sync(kFull, excl, L);
+            const int cl = __shfl_sync(kFull, cnt, L);
+            const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
+            if (e < tot_in) {
+                const unsigned long long* row = keys + L * kRowStride;
+                const unsigned long long kk = row[e - xin];
+                if (kk != self_key) {
+                    int rank = (self_key < kk) ? -1 : 0;
+                    for (int y = 0; y < nl; ++y) rank += row[y] < kk;
+                    if (rank < cl) {
+                        st.pool[base_off + ol + rank] = (int)(unsigned)kk;
+                        if (emit) st.pool_d2[base_off + ol + rank] = __uint_as_float((unsigned)(kk >> 32));
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // Stage 5: count every query's neighbours; rows of at most kFast neighbours
 // are also collected, sorted, cut at k and written to the pool (space taken
 // per chunk from a counter), so that stage 7 only copies them.
@@ -1423,10 +1514,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
-    const int K = st.hdr->k;
     const int B = st.hdr->n_events;
-    const int emit = st.hdr->emit_d2;
-    const long long pool_cap = st.hdr->edge_capacity;
     const long long nchunks = (P + 31) >> 5;
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
     LaneEvent le;
@@ -1498,69 +1586,225 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                     }
                 });
             }
-            // pool space for the chunk's short rows
-            const int raw = deg;                 // includes the query itself
-            deg = raw > 0 ? raw - 1 : 0;         // |S_i|
-            const int cnt = min(deg, K);
-            const bool fast = valid && deg > 0 && deg <= kFast;
-            const int need = fast ? cnt : 0;
-            const int incl = warp_incl_scan(need, lane);
-            const int tot = __shfl_sync(kFull, incl, 31);
-            unsigned long long base_off = 0ull;
-            if (lane == 0 && tot > 0) base_off = atomicAdd(st.pool_ctr, (unsigned long long)tot);
-            base_off = __shfl_sync(kFull, base_off, 0);
-            const bool fits = (long long)(base_off + (unsigned long long)tot) <= pool_cap;
-            const int my_off = (fast && fits) ? (int)(base_off + (unsigned long long)(incl - need)) : -1;
-            const int self_j = valid ? __ldg(st.perm + q) : -1;
-            if (valid) {
-                st.pool_off[le.pt_off + self_j] = my_off;
-                st.cnt_o[le.pt_off + self_j] = cnt;
+            park_rows<false>(st, keys, deg, valid, q, le, lane);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 5, query-major form (dimensions up to 12).
+//
+// A lane per query.  The chunk's segments (queries sharing a cell) first list
+// their non-empty runs of neighbouring cells in shared memory, as many
+// segments at a time as the list holds; then every lane streams its own
+// segment's candidates, two per step, against its query held in registers.
+// Unlike the candidate-major walk there is no vote, shuffle or slot
+// arithmetic per test: a hit is one predicated shared-memory store into the
+// lane's own row.  The price is the spread of candidate counts between the
+// chunk's segments (a lane whose segment has fewer candidates idles at the
+// end).  Rows, the pool and the emit walk's list come out as in the
+// candidate-major walk; keys carry the candidate's sorted position until the
+// row is parked.
+
+constexpr int kRunCap = 256;  // run-list entries per warp
+static_assert(kRunCap >= kMaxRuns, "the runs of any one segment must fit the run list");
+// 8-byte words of shared memory per warp: rows, run list, segment bounds
+constexpr int kQWarpWords = 32 * kRowStride + kRunCap + 32;
+
+// Appends the non-empty runs of the segment whose cell coordinates are in
+// ww.ks to runs[cnt ..] as (first, end) sorted positions, in run order.
+// Returns false, with cnt unchanged, if they do not all fit the list.
+__device__ __forceinline__ bool append_runs(const WarpWalk& ww, const int2* run_tab, const int* cell_start,
+                                            int lane, int2* runs, int& cnt)
+{
+    const EvPlan& pl = ww.pl;
+    const int g = pl.g;
+    const int nr = n_runs(g);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (nr <= 32) {
+        int beg = 0, len = 0;
+        if (lane < nr) run_of(ww, lane, cell_start, beg, len);
+        const unsigned m = __ballot_sync(kFull, len > 0);
+        if (cnt + __popc(m) > kRunCap) return false;
+        if (len > 0) runs[cnt + __popc(m & lt_mask)] = make_int2(beg, beg + len);
+        cnt += __popc(m);
+        return true;
+    }
+    // five or six gridded dims: offsets and face masks from the event's run
+    // table (as in for_each_run_group)
+    int cb = 0, bad = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxG - 1; ++t) {
+        if (t < g - 1) {
+            const int kt = ww.ks[t];
+            cb += kt * pl.stride[t];
+            if (kt == 0) bad |= 1 << t;
+            if (kt == pl.ncell[t] - 1) bad |= 1 << (5 + t);
+        }
+    }
+    const int kl = ww.ks[g - 1], ncl = pl.ncell[g - 1];
+    const int* cs_lo = cell_start + pl.cell_off + cb + max(kl - 1, 0);
+    const int* cs_hi = cell_start + pl.cell_off + cb + min(kl + 1, ncl - 1) + 1;
+    int n = cnt;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int ri = r0 + lane;
+        int beg = 0, len = 0;
+        if (ri < nr) {
+            const int2 rt = __ldg(run_tab + ri);
+            if ((rt.y & bad) == 0) {
+                beg = __ldg(cs_lo + rt.x);
+                len = __ldg(cs_hi + rt.x) - beg;
             }
-            // rows that were not parked go on the emit walk's list
-            const bool longrow = valid && cnt > 0 && my_off < 0;
-            const unsigned lm = __ballot_sync(kFull, longrow);
-            if (lm) {
-                unsigned lbase = 0;
-                if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
-                lbase = __shfl_sync(kFull, lbase, 0);
-                if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
-            }
-            __syncwarp();
-            // The parked rows go to the pool sorted and cut at k: they fill
-            // [base_off, base_off + tot) in lane order.  The warp streams the
-            // rows' collected keys (the query's own key included) flat, each key
-            // finding its row by binary lifting over the lanes' prefix sums; a
-            // key's place in its row is the number of the row's keys below it,
-            // less one if the query's own key (d2 = 0, j = itself) is among them.
-            if (fits) {
-                const int nin = my_off >= 0 ? raw : 0;
-                const int incl_in = warp_incl_scan(nin, lane);
-                const int tot_in = __shfl_sync(kFull, incl_in, 31);
-                const int excl_in = incl_in - nin;
-                const int excl = incl - need;
-                for (int e0 = 0; e0 < tot_in; e0 += 32) {
-                    const int e = e0 + lane;
-                    const int L = find_run(incl_in, e);
-                    const int xin = __shfl_sync(kFull, excl_in, L);
-                    const int nl = __shfl_sync(kFull, nin, L);
-                    const int ol = __shfl_sync(kFull, excl, L);
-                    const int cl = __shfl_sync(kFull, cnt, L);
-                    const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
-                    if (e < tot_in) {
-                        const unsigned long long* row = keys + L * kRowStride;
-                        const unsigned long long kk = row[e - xin];
-                        if (kk != self_key) {
-                            int rank = (self_key < kk) ? -1 : 0;
-                            for (int y = 0; y < nl; ++y) rank += row[y] < kk;
-                            if (rank < cl) {
-                                st.pool[base_off + ol + rank] = (int)(unsigned)kk;
-                                if (emit) st.pool_d2[base_off + ol + rank] = __uint_as_float((unsigned)(kk >> 32));
+        }
+        const unsigned m = __ballot_sync(kFull, len > 0);
+        if (n + __popc(m) > kRunCap) return false;
+        if (len > 0) runs[n + __popc(m & lt_mask)] = make_int2(beg, beg + len);
+        n += __popc(m);
+    }
+    cnt = n;
+    return true;
+}
+
+// d2 of a query against a candidate row, both as pairs of dims (a float4 is
+// two pairs): each pair is subtracted and squared as one packed operation
+// (two IEEE single operations), and the squares are added one at a time in
+// dim order, so the value equals the sequential float32 sum bit for bit.
+template <int DP4>
+__device__ __forceinline__ float dist2_rows(const ulonglong2 (&qv)[DP4], const ulonglong2 (&cv)[DP4])
+{
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < DP4; ++k) {
+        const unsigned long long a = pk_sqr(pk_sub(qv[k].x, cv[k].x));  // dims 4k, 4k+1
+        const unsigned long long b = pk_sqr(pk_sub(qv[k].y, cv[k].y));  // dims 4k+2, 4k+3
+        s = (k == 0) ? __uint_as_float((unsigned)a) : __fadd_rn(s, __uint_as_float((unsigned)a));
+        s = __fadd_rn(s, __uint_as_float((unsigned)(a >> 32)));
+        s = __fadd_rn(s, __uint_as_float((unsigned)b));
+        s = __fadd_rn(s, __uint_as_float((unsigned)(b >> 32)));
+    }
+    return s;
+}
+
+template <int DP4>
+__global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
+{
+    if (timed_out(st)) return;
+    extern __shared__ unsigned long long s_qwords[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned long long* keys = s_qwords + (size_t)wib * kQWarpWords;
+    int2* runs = reinterpret_cast<int2*>(keys + 32 * kRowStride);
+    int2* segb = runs + kRunCap;  // per segment (indexed by its first lane): its entries of the run list
+    unsigned long long* my_row = keys + lane * kRowStride;
+    const long long P = st.hdr->n_total;
+    const float r2 = st.hdr->r2;
+    const int B = st.hdr->n_events;
+    const long long nchunks = (P + 31) >> 5;
+    const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
+    LaneEvent le;
+    le.lo = 1;
+    le.hi = 0;
+    __shared__ WarpWalk s_ww[kWalkThreads / 32];
+    WarpWalk& ww = s_ww[wib];
+    int plan_b = -1;
+    const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
+    const unsigned group = nchunks >= 4 * nwarps ? (unsigned)kChunkGroup : 1u;
+    for (;;) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(&st.counters[kCtrWalkChunks], group);
+        g0 = __shfl_sync(kFull, g0, 0);
+        if ((long long)g0 >= nchunks) break;
+        const long long gend = min((long long)g0 + group, nchunks);
+        for (long long ch = g0; ch < gend; ++ch) {
+            const long long q = (ch << 5) + lane;
+            const bool valid = q < P;
+            lane_event(st.ev, B, valid ? q : P - 1, le);
+            const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
+            ulonglong2 qv[DP4];
+#pragma unroll
+            for (int k = 0; k < DP4; ++k) qv[k] = __ldg(xs2 + (valid ? q : 0) * DP4 + k);
+            // segments: runs of lanes with the same cell and event
+            const unsigned up_cs = __shfl_up_sync(kFull, cs, 1);
+            const int up_b = __shfl_up_sync(kFull, le.b, 1);
+            const bool start = valid && (lane == 0 || cs != up_cs || le.b != up_b);
+            const unsigned segm = __ballot_sync(kFull, start);
+            const int my_a = 31 - __clz(segm & (kFull >> (31 - lane)));  // first lane of this lane's segment
+            int deg = 0;
+            unsigned todo = segm;
+            while (todo) {
+                // list the runs of as many segments as fit (the first always does)
+                unsigned batch = 0;
+                int cnt = 0;
+                while (todo) {
+                    const int a = __ffs(todo) - 1;
+                    const int sb = __shfl_sync(kFull, le.b, a);
+                    const unsigned csa = __shfl_sync(kFull, cs, a);
+                    if (sb != plan_b) {
+                        load_plan(ww, st.plan, sb, lane);
+                        plan_b = sb;
+                    }
+                    const int lo_r = cnt;
+                    if (!ww.pl.skip) {
+                        // the segment's cell coordinates, from its cell id
+                        if (lane < ww.pl.g)
+                            ww.ks[lane] = (int)((csa / (unsigned)ww.pl.stride[lane]) % (unsigned)ww.pl.ncell[lane]);
+                        __syncwarp();
+                        if (!append_runs(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, runs, cnt))
+                            break;
+                    }
+                    if (lane == 0) segb[a] = make_int2(lo_r, cnt);
+                    batch |= 1u << a;
+                    todo &= todo - 1;
+                }
+                __syncwarp();
+                // every lane of the batch streams its segment's candidates
+                int li = 0, hi = 0, pos = 0, end = 0;
+                if (valid && ((batch >> my_a) & 1u)) {
+                    const int2 sbd = segb[my_a];
+                    li = sbd.x;
+                    hi = sbd.y;
+                }
+                bool act = li < hi;
+                if (act) {
+                    const int2 rr = runs[li];
+                    pos = rr.x;
+                    end = rr.y;
+                }
+                while (__any_sync(kFull, act)) {
+                    if (act) {
+                        const bool two = pos + 1 < end;
+                        const ulonglong2* ra = xs2 + (long long)pos * DP4;
+                        const ulonglong2* rb = two ? ra + DP4 : ra;
+                        ulonglong2 ca[DP4], cb[DP4];
+#pragma unroll
+                        for (int k = 0; k < DP4; ++k) ca[k] = __ldg(ra + k);
+#pragma unroll
+                        for (int k = 0; k < DP4; ++k) cb[k] = __ldg(rb + k);
+                        const float da = dist2_rows<DP4>(qv, ca);
+                        const float db = dist2_rows<DP4>(qv, cb);
+                        if (da <= r2) {
+                            if (deg < kRowSlots) my_row[deg] = edge_key(da, pos);
+                            ++deg;
+                        }
+                        if (two && db <= r2) {
+                            if (deg < kRowSlots) my_row[deg] = edge_key(db, pos + 1);
+                            ++deg;
+                        }
+                        pos += 2;
+                        if (pos >= end) {
+                            if (++li < hi) {
+                                const int2 rr = runs[li];
+                                pos = rr.x;
+                                end = rr.y;
+                            } else {
+                                act = false;
                             }
                         }
                     }
                 }
+                __syncwarp();  // the run list is rewritten for the next batch
             }
-            __syncwarp();
+            park_rows<true>(st, keys, deg, valid, q, le, lane);
         }
     }
 }
@@ -2016,16 +2260,29 @@ int collect_smem()
 }
 
 template <int DP4>
+int collect_q_smem()
+{
+    return (kWalkThreads / 32) * kQWarpWords * (int)sizeof(unsigned long long);
+}
+
+template <int DP4>
 int emit_smem(int cap)
 {
     return (kFillThreads / 32) * (2 * 4 * DP4 * (int)sizeof(float) + 2 * cap * (int)sizeof(unsigned long long));
 }
 
 template <int DP4>
-cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, cudaStream_t s, cudaEvent_t* ev)
+cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, int walk, cudaStream_t s, cudaEvent_t* ev)
 {
     mark(ev, 4, s);
-    k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+    if constexpr (DP4 <= 3) {
+        if (walk == kWalkQueryMajor)
+            k_walk_collect_q<DP4><<<cfg.grid_count_q, kWalkThreads, collect_q_smem<DP4>(), s>>>(st);
+        else
+            k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+    } else {
+        k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+    }
     mark(ev, 5, s);
     k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 6, s);
@@ -2048,9 +2305,17 @@ cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_walk_knn<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
     if (e != cudaSuccess) return e;
-    int nb_c = 0, nb_f = 0;
+    int nb_c = 0, nb_f = 0, nb_q = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4>, kWalkThreads, csm);
     if (e != cudaSuccess) return e;
+    if constexpr (DP4 <= 3) {
+        const int qsm = collect_q_smem<DP4>();
+        e = cudaFuncSetAttribute(k_walk_collect_q<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, qsm);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_q, k_walk_collect_q<DP4>, kWalkThreads, qsm);
+        if (e != cudaSuccess) return e;
+    }
+    cfg->grid_count_q = n_sm * (nb_q > 0 ? nb_q : 1);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_f, k_walk_emit<DP4>, kFillThreads, fsm);
     if (e != cudaSuccess) return e;
     cfg->grid_count = n_sm * (nb_c > 0 ? nb_c : 1);
@@ -2072,7 +2337,7 @@ cudaError_t launch_knn_walk(const DevState& st, const LaunchCfg& cfg, cudaStream
 
 #define FRNN_DP4_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
-int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream, void* stage_events)
+int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, int walk, void* stream, void* stage_events)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t* ev = static_cast<cudaEvent_t*>(stage_events);
@@ -2087,7 +2352,7 @@ int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     switch (dp4) {
-#define FRNN_CASE(n) case n: return (int)launch_walks<n>(st, cfg, s, ev);
+#define FRNN_CASE(n) case n: return (int)launch_walks<n>(st, cfg, walk, s, ev);
         FRNN_DP4_CASES(FRNN_CASE)
 #undef FRNN_CASE
         default: return (int)cudaErrorInvalidValue;

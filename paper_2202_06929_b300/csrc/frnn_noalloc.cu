@@ -132,6 +132,16 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     LaunchCfg cfg;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!ds->base || !ds->cfg_ok[dp4]) {
+            // The set-up below makes calls that are not stream-ordered; under
+            // stream capture they would fail or invalidate the capture, so a
+            // set-up call on a capturing stream is refused before any of them.
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+                cudaGetLastError();
+                return FRNN_ERR_INVALID_ARG;
+            }
+        }
         if (!ds->base) {
             // Host code must not use g_noalloc_scratch directly (its host-side
             // name is not a device address): fetch the address once per device.
@@ -217,12 +227,17 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
         return FRNN_OK;
     }
     const long long cap_edges = n * (long long)k_max;
+    // points per chunk of the per-point kernels: as for a plan's build, the
+    // smallest power of two from kChunkMin that leaves at most about two
+    // chunks per block, so that a small event still spreads over the SMs
+    int chunk = kChunkMin;
+    while (chunk < kChunk && (n + chunk - 1) / chunk > 2ll * cfg.grid_pt) chunk *= 2;
     CallHdr h{};
     h.emb = emb;
     h.n_total = n;
     h.n_events = 1;
-    h.total_chunks = (int)((n + kChunk - 1) / kChunk);
-    h.chunk = kChunk;
+    h.total_chunks = (int)((n + chunk - 1) / chunk);
+    h.chunk = chunk;
     h.d = d;
     h.dp = dp4 * 4;
     h.k = k_max;
@@ -241,7 +256,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     k_noalloc_header<<<1, 32, 0, s>>>(h, e, reinterpret_cast<CallHdr*>(b + kOffHdr),
                                       reinterpret_cast<EvDesc*>(b + kOffEv));
     if (cudaGetLastError() != cudaSuccess) return FRNN_ERR_CUDA;
-    if (launch_build(st, dp4, cfg, s, nullptr) != 0) {
+    if (launch_build(st, dp4, cfg, resolve_walk(kWalkAuto, dp4), s, nullptr) != 0) {
         cudaGetLastError();
         return FRNN_ERR_CUDA;
     }

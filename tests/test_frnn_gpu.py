@@ -3,8 +3,12 @@
 Every comparison is exact: row_ptr and col equal element by element (and d2
 bit for bit when emitted).  The CUDA path computes each squared distance with
 the same float32 operations in the same order as the oracle, so the edge sets
-agree on any input, on the 1/256 grid or off it.
+agree on any input, on the 1/256 grid or off it.  Both forms of the
+neighbour walk (candidates across the lanes, or a lane per query) are
+checked on the seeded sweep, the tunings and the full-size events.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -15,6 +19,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2202_06929_b300 as frnn  # noqa: E402
+
+WALKS = [frnn._native.FRNN_WALK_CANDIDATES, frnn._native.FRNN_WALK_QUERIES]
+WALK_IDS = ["cand", "query"]
 
 
 def gpu_csr(x, r, k, emit_d2=False, use_graph=False, tuning=None, plan=None, cells_per_point=0):
@@ -98,23 +105,34 @@ def _make(kind, n, d, seed):
     return synth.duplicates(n, d, seed, max(n // 20, 1))
 
 
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
 @pytest.mark.parametrize("case,n,d,k,kind,r", SWEEP, ids=[f"c{c[0]}-n{c[1]}-d{c[2]}-k{c[3]}-{c[4]}" for c in SWEEP])
-def test_property_sweep(case, n, d, k, kind, r):
+def test_property_sweep(case, n, d, k, kind, r, walk):
     x = _make(kind, n, d, 1000 + case)
-    assert_same_as_oracle(x, r, k)
+    assert_same_as_oracle(x, r, k, tuning=(0, 0.0, walk))
 
 
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
 @pytest.mark.parametrize("g_max,scale", [(1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0), (4, 1.5), (3, 2.0), (2, 3.7),
                                          (5, 1.0), (6, 1.0), (6, 1.5), (5, 2.0)])
-def test_tuning_never_changes_result(g_max, scale):
+def test_tuning_never_changes_result(g_max, scale, walk):
     # a cell budget large enough for five and six gridded dims (81 and 243 runs per cell)
     x = synth.clustered_grid(4000, 8, 5, 300, 0.03, 0.15)
-    assert_same_as_oracle(x, 0.1, 16, tuning=(g_max, scale), cells_per_point=512)
+    assert_same_as_oracle(x, 0.1, 16, tuning=(g_max, scale, walk), cells_per_point=512)
 
 
-def test_six_gridded_dims_high_dimensional_event():
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
+def test_six_gridded_dims_high_dimensional_event(walk):
     x = synth.clustered_grid(20000, 12, 8, 1500, 0.03, 0.25)
-    assert_same_as_oracle(x, 0.15, 40, tuning=(6, 1.0), cells_per_point=256)
+    assert_same_as_oracle(x, 0.15, 40, tuning=(6, 1.0, walk), cells_per_point=256)
+
+
+def test_query_major_run_list_overflow():
+    """Dense single-point cells: a 32-query chunk holds up to 32 segments of
+    27 non-empty runs each, more than one run list holds, so the lane-per-query
+    walk takes the chunk's segments in several batches."""
+    x = synth.uniform_grid(6000, 4, 31, -256, 256)
+    assert_same_as_oracle(x, 0.18, 64, tuning=(4, 1.0, frnn._native.FRNN_WALK_QUERIES))
 
 
 # ------------------------------------------------------------------ edge cases
@@ -285,14 +303,25 @@ def _check_sampled(x, r, k, host_rp, host_col, queries):
         np.testing.assert_array_equal(got, want, err_msg=f"row {i}")
 
 
-def test_c2_full_event_sampled_rows_and_symmetry():
-    """N=120,000, D=8, r=0.1, K=256: sampled rows exact; the cap never binds at
-    this density, so the whole graph must be symmetric."""
+@functools.lru_cache(maxsize=8)
+def _c2_oracle(event):
+    """The whole oracle graph of event `event` of the N=120,000 workload
+    (every row; about 8 s on 16 host cores)."""
+    return oracle.radius_graph(synth.make_event("c2", event), 0.1, 256)
+
+
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
+def test_c2_full_event_every_row(walk):
+    """N=120,000, D=8, r=0.1, K=256: the whole graph (row_ptr and every col
+    entry) equals the oracle's; the cap never binds at this density, so the
+    graph is also symmetric and every edge lies within r."""
     x = synth.make_event("c2")
-    host, st = gpu_csr(x, 0.1, 256, use_graph=True)
+    host, st = gpu_csr(x, 0.1, 256, use_graph=True, tuning=(0, 0.0, walk))
     assert st == 0
+    orp, ocol = _c2_oracle(0)
     rp, col = host["row_ptr"].astype(np.int64), host["col"]
-    _check_sampled(x, 0.1, 256, rp, col, _sample_queries(x.shape[0], 3000, 1))
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(col, ocol)
     n = x.shape[0]
     src = np.repeat(np.arange(n), np.diff(rp))
     a = src.astype(np.int64) * n + col
@@ -305,20 +334,29 @@ def test_c2_full_event_sampled_rows_and_symmetry():
     assert np.all(d2 * 65536 <= oracle.grid_threshold(0.1))
 
 
-def test_c2_batched_bench_configuration():
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
+def test_c2_batched_bench_configuration(walk):
     """The benchmark's configuration: 64 events of N=120,000 (seeded per event),
-    one batched build replayed from a CUDA graph; sampled rows of every event."""
+    one batched build replayed from a CUDA graph: every row of four events
+    (first, last and two between) equals the oracle's, and sampled rows of
+    every third event."""
     n_ev = 64
     evs = [synth.make_event("c2", e) for e in range(n_ev)]
     off = np.concatenate([[0], np.cumsum([e.shape[0] for e in evs])]).astype(np.int64)
     allx = torch.from_numpy(np.concatenate(evs)).cuda()
     plan = frnn.Plan(n_max=int(off[-1]), d_max=8, k_max_cap=256, events_max=n_ev,
-                     edge_capacity=int(off[-1]) * 64, use_graph=True)
+                     edge_capacity=int(off[-1]) * 64, cells_per_point=32, use_graph=True)
     try:
+        plan.set_tuning(4, 1.0, walk)
         for rep in range(2):
             csr = plan.build_batched(allx, off, 0.1, 256)
             host = csr.to_host()
             assert plan.last_status() == 0
+        for b in (0, 21, 42, 63):
+            rp, col = csr.event_rows(host, b)
+            orp, ocol = _c2_oracle(b)
+            np.testing.assert_array_equal(rp, orp, err_msg=f"event {b}")
+            np.testing.assert_array_equal(col, ocol, err_msg=f"event {b}")
         for b in range(0, n_ev, 3):
             rp, col = csr.event_rows(host, b)
             _check_sampled(evs[b], 0.1, 256, rp, col, _sample_queries(evs[b].shape[0], 150, b))

@@ -65,3 +65,44 @@ def test_noalloc_refuses_sizes_beyond_its_limits():
     for n, d, k in [(32769, 4, 8), (100, 17, 8), (100, 4, 65)]:
         rc = fn(x.data_ptr(), n, d, 0.1, k, rp.data_ptr(), col.data_ptr(), 16, st.data_ptr(), None)
         assert rc == frnn.FRNN_ERR_CAPACITY
+
+
+def test_noalloc_device_status_outputs_and_empty_event():
+    """The device-side outcomes: more edges than col_capacity gives OVERFLOW,
+    a NaN gives NONFINITE_INPUT with empty rows, and n = 0 gives row_ptr[0] = 0
+    with status OK."""
+    fn = _entry()
+    stream = torch.cuda.current_stream().cuda_stream
+    x = synth.make_event("c1")
+    n, d = x.shape
+    ref = _reference(x, 0.1, 64)
+    xt = torch.from_numpy(x).cuda()
+    row_ptr = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    col = torch.zeros(n * 64, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    small = int(ref["row_ptr"][-1]) - 1
+    rc = fn(xt.data_ptr(), n, d, 0.1, 64, row_ptr.data_ptr(), col.data_ptr(), small, status.data_ptr(), stream)
+    assert rc == frnn.FRNN_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == frnn.FRNN_ERR_OVERFLOW
+    bad = x.copy()
+    bad[5, 1] = np.nan
+    bt = torch.from_numpy(bad).cuda()
+    rc = fn(bt.data_ptr(), n, d, 0.1, 64, row_ptr.data_ptr(), col.data_ptr(), col.numel(), status.data_ptr(), stream)
+    assert rc == frnn.FRNN_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == frnn.FRNN_ERR_NONFINITE_INPUT
+    assert int(row_ptr[-1].item()) == 0
+    row_ptr.fill_(-3)
+    status.fill_(-1)
+    rc = fn(xt.data_ptr(), 0, d, 0.1, 64, row_ptr.data_ptr(), col.data_ptr(), col.numel(), status.data_ptr(), stream)
+    assert rc == frnn.FRNN_OK
+    torch.cuda.synchronize()
+    assert int(row_ptr[0].item()) == 0 and int(status.item()) == frnn.FRNN_OK
+    # and the next call is exact again
+    rc = fn(xt.data_ptr(), n, d, 0.1, 64, row_ptr.data_ptr(), col.data_ptr(), col.numel(), status.data_ptr(), stream)
+    assert rc == frnn.FRNN_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == frnn.FRNN_OK
+    np.testing.assert_array_equal(row_ptr.cpu().numpy(), ref["row_ptr"])
+    np.testing.assert_array_equal(col[: int(ref["row_ptr"][-1])].cpu().numpy(), ref["col"])
