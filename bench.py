@@ -48,7 +48,9 @@ STAGES = ("bbox_plan", "key_hist", "scan_cells", "scatter", "walk_collect", "sca
 L2_BYTES = 126 * 1024 * 1024
 KFAST_ROWS = 24  # rows longer than this are walked a second time by the emit walk
 KNN_K = 16       # k of the exact-kNN measurement
-AUTOTUNE_SPACE = "g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}, best of 3 builds each"
+AUTOTUNE_SPACE = ("20 grids (g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}) probed for their exact "
+                  "candidate tests, non-empty cells and cell slots; the 3 cheapest timed with both walk forms "
+                  "(best of 3 builds)")
 # DRAM read + write bytes per point and warp instructions per query of the
 # collect walk, from one ncu capture of the N=120k workload (40 events, 4.8 M
 # points); valid only for the kernel code it was taken on (the sha1 of the

@@ -67,6 +67,8 @@ typedef enum {
 /* Plan flags. */
 #define FRNN_EMIT_D2 0x1u    /* also write the float32 d2 of every edge              */
 #define FRNN_USE_GRAPH 0x2u  /* replay the build as a CUDA graph captured on first use */
+#define FRNN_AUTOTUNE 0x4u   /* a radius build whose call shape has no autotuned entry
+                                yet runs frnn_plan_autotune first (synchronously)      */
 
 typedef struct frnn_plan frnn_plan; /* opaque; owns all device scratch and outputs */
 
@@ -78,7 +80,7 @@ typedef struct {
     int k_max_cap;         /* largest neighbour cap of one call, 1..1024              */
     int64_t edge_capacity; /* col slots; 0 = n_max * k_max_cap (never overflows)      */
     int cells_per_point;   /* cell-table slots per point (plus 4096 per event); 0 = 4 */
-    uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH                           */
+    uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH | FRNN_AUTOTUNE           */
 } frnn_plan_params;
 
 /*
@@ -143,22 +145,38 @@ FRNN_API int frnn_plan_bytes(const frnn_plan_params* p, uint64_t* bytes);
 /* Free every buffer of the plan (synchronises its device).  NULL is a no-op. */
 FRNN_API int frnn_plan_destroy(frnn_plan* plan);
 
-/* Set / read the cell-grid tuning used by the following builds. */
+/*
+ * Set / read the plan's tuning, used by builds whose call shape has no
+ * autotuned entry.  Setting it also drops every autotuned entry.
+ */
 FRNN_API int frnn_plan_set_tuning(frnn_plan* plan, const frnn_tuning* t);
 FRNN_API int frnn_plan_get_tuning(const frnn_plan* plan, frnn_tuning* t);
 
 /*
- * Autotune the cell grid for a workload (the choice of gridded dimensions the
- * paper makes by hand, Sec. 3.4): times the batched build of the given events
- * for g_max in {6, 5, 4, 3, 2} x cell_scale in {1, 1.25, 1.5, 2} (best of three
- * builds each, after one warm-up), sets the fastest on the plan, and returns
- * it in *best and its time in *best_ms (either may be NULL).  Synchronous.
- * Results never depend on the tuning, only the speed does.  Arguments and
- * errors as frnn_build_graph_batched.
+ * Autotune for a workload (the choice of gridded dimensions the paper makes by
+ * hand, Sec. 3.4, and the form of the walk).  Each of the 20 grids g_max in
+ * {6, 5, 4, 3, 2} x cell_scale in {1, 1.25, 1.5, 2} is probed on the given
+ * events (the grid stages and an exact count of the candidate tests, non-empty
+ * cells and cell slots a build would handle, no edges written); the three
+ * cheapest by that count are timed with each walk form (best of three builds
+ * after a warm-up).  The fastest tuning becomes the plan's tuning and the
+ * entry for the call's shape (mean points per event, number of events, d, r,
+ * k_max; a plan keeps the last 16 shapes), and is returned in *best with its
+ * time in *best_ms (either may be NULL).  Synchronous.  Results never depend
+ * on the tuning, only the speed does.  Arguments and errors as
+ * frnn_build_graph_batched; the plan's last build is not kept.
  */
 FRNN_API int frnn_plan_autotune(frnn_plan* plan, const float* emb, const int64_t* ev_off, int n_events,
                                 int d, float r, int k_max, void* stream, frnn_tuning* best,
                                 float* best_ms);
+
+/*
+ * The tuning a build with these arguments would use: the autotuned entry for
+ * its shape (*cached = 1) or the plan's tuning (*cached = 0; cached may be
+ * NULL).  Host only.  Errors: INVALID_ARG.
+ */
+FRNN_API int frnn_plan_tuning_for(const frnn_plan* plan, const int64_t* ev_off, int n_events, int d, float r,
+                                  int k_max, frnn_tuning* out, int* cached);
 
 /*
  * Build the graph of one event (Sec. 2, Sec. 3.4; the cap of Sec. 3.1).
@@ -189,7 +207,8 @@ FRNN_API int frnn_build_graph_batched(frnn_plan* plan, const float* emb, const i
 
 /*
  * Host-to-host form (the whole call a CPU-side user makes): copies the
- * events' points from host memory to the device, builds, and copies the CSR
+ * events' points from host memory to the device (into a buffer of n_max x
+ * d_max floats the plan reserves at creation), builds, and copies the CSR
  * back.  Synchronous: returns when the host buffers are filled.
  *   h_emb       host float32 [ev_off[n_events]][d] (pinned memory is faster).
  *   h_row_ptr   host int32 [ev_off[n_events] + 1], receives row_ptr.

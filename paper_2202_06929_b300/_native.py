@@ -26,6 +26,7 @@ FRNN_ERR_CAPACITY = 7
 FRNN_NO_CAP = 0   # k = FRNN_NO_CAP keeps every row whole (rows over 24 neighbours unsorted)
 FRNN_EMIT_D2 = 0x1
 FRNN_USE_GRAPH = 0x2
+FRNN_AUTOTUNE = 0x4
 
 # Every function the header declares (checked by the tests against the .so).
 ABI_FUNCTIONS = (
@@ -35,7 +36,7 @@ ABI_FUNCTIONS = (
     "frnn_plan_bytes", "frnn_server_create", "frnn_server_reserved_bytes", "frnn_server_submit",
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
     "frnn_label_components", "frnn_edge_features", "frnn_knn_graph_batched",
-    "frnn_plan_test_stall_next_build", "frnn_server_poll", "frnn_server_get_stats",
+    "frnn_plan_test_stall_next_build", "frnn_server_poll", "frnn_server_get_stats", "frnn_plan_tuning_for",
 )
 
 
@@ -109,6 +110,7 @@ def load():
     lib.frnn_server_submit.argtypes = [vp, vp, i64, P(ctypes.c_uint64)]
     lib.frnn_server_wait.argtypes = [vp, ctypes.c_uint64, vp, vp, i64, P(ctypes.c_int64), P(ctypes.c_double)]
     lib.frnn_server_poll.argtypes = [vp, ctypes.c_uint64, P(ctypes.c_int)]
+    lib.frnn_plan_tuning_for.argtypes = [vp, P(ctypes.c_int64), i32, i32, f32, i32, P(frnn_tuning), P(ctypes.c_int)]
     lib.frnn_server_get_stats.argtypes = [vp, P(frnn_server_stats)]
     lib.frnn_server_run_trace.argtypes = [vp, vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_double), i32,
                                           P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double)]
@@ -234,12 +236,13 @@ class Plan:
 
     def __init__(self, n_max: int, d_max: int, k_max_cap: int, events_max: int = 1,
                  edge_capacity: int = 0, cells_per_point: int = 0, emit_d2: bool = False,
-                 use_graph: bool = False, device: int = 0):
+                 use_graph: bool = False, device: int = 0, autotune: bool = False):
         lib = load()
         prm = frnn_plan_params(device=device, d_max=d_max, n_max=n_max, events_max=events_max,
                                k_max_cap=k_max_cap, edge_capacity=edge_capacity,
                                cells_per_point=cells_per_point,
-                               flags=(FRNN_EMIT_D2 if emit_d2 else 0) | (FRNN_USE_GRAPH if use_graph else 0))
+                               flags=((FRNN_EMIT_D2 if emit_d2 else 0) | (FRNN_USE_GRAPH if use_graph else 0)
+                                      | (FRNN_AUTOTUNE if autotune else 0)))
         h = ctypes.c_void_p()
         _check(lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)), "frnn_plan_create")
         self._h = h
@@ -278,6 +281,17 @@ class Plan:
         t = frnn_tuning()
         _check(load().frnn_plan_get_tuning(self._h, ctypes.byref(t)), "frnn_plan_get_tuning")
         return int(t.g_max), float(t.cell_scale), int(t.walk)
+
+    def tuning_for(self, ev_off, d: int, r: float, k: int) -> tuple[int, float, int, bool]:
+        """(g_max, cell_scale, walk, cached): the tuning a build with these
+        arguments would use, and whether it is an autotuned entry."""
+        off = np.ascontiguousarray(ev_off, dtype=np.int64)
+        t = frnn_tuning()
+        c = ctypes.c_int(0)
+        _check(load().frnn_plan_tuning_for(self._h, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           off.size - 1, int(d), float(r), int(k), ctypes.byref(t),
+                                           ctypes.byref(c)), "frnn_plan_tuning_for")
+        return int(t.g_max), float(t.cell_scale), int(t.walk), bool(c.value)
 
     def autotune(self, emb, ev_off, r: float, k: int, stream=None) -> tuple[int, float, float]:
         """frnn_plan_autotune on this batch: returns (g_max, cell_scale, ms) of

@@ -2,6 +2,7 @@
 // CUDA-graph replay of a build.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -38,6 +39,36 @@ int next_pow2(int v)
     int p = 1;
     while (p < v) p <<= 1;
     return p;
+}
+
+// The shape of a call that a tuning is cached for: mean points per event
+// (two buckets per octave), events (one per octave), dimension, radius, cap.
+struct TuneKey {
+    int n_bucket = -1, ev_bucket = -1, d = 0, k = 0;
+    float r = 0.f;
+    bool operator==(const TuneKey& o) const
+    {
+        return n_bucket == o.n_bucket && ev_bucket == o.ev_bucket && d == o.d && k == o.k && r == o.r;
+    }
+};
+
+struct TuneEntry {
+    TuneKey key;
+    frnn_tuning t{};
+};
+
+constexpr int kTuneCache = 16;
+
+TuneKey tune_key(const int64_t* ev_off, int n_events, int d, float r, int k)
+{
+    TuneKey key;
+    const double mean = (double)ev_off[n_events] / (double)n_events;
+    key.n_bucket = mean >= 1.0 ? (int)std::floor(2.0 * std::log2(mean)) : -1;
+    key.ev_bucket = (int)std::floor(std::log2((double)n_events));
+    key.d = d;
+    key.k = k;
+    key.r = r;
+    return key;
 }
 
 struct GraphEntry {
@@ -83,9 +114,44 @@ struct frnn_plan {
     int last_d = 0;
     bool has_last = false;
     bool stall_next = false;  // frnn_plan_test_stall_next_build
+    // autotuner: probe output (device, 3 x u64) and the tunings it found,
+    // keyed by the shape of the call
+    unsigned long long* probe = nullptr;
+    TuneEntry tune_cache[kTuneCache];
+    int n_tune = 0, tune_next = 0;
+    bool tuning_fixed = false;  // the autotuner is timing p->tuning itself: no lookup
 };
 
 namespace {
+
+// The tuning a call uses: the autotuner's entry for the call's shape if there
+// is one, else the plan's tuning.
+frnn_tuning tuning_for(const frnn_plan* p, const int64_t* ev_off, int n_events, int d, float r, int k,
+                       bool* cached = nullptr)
+{
+    if (cached) *cached = false;
+    if (!p->tuning_fixed && p->n_tune > 0) {
+        const TuneKey key = tune_key(ev_off, n_events, d, r, k);
+        for (int i = 0; i < p->n_tune; ++i)
+            if (p->tune_cache[i].key == key) {
+                if (cached) *cached = true;
+                return p->tune_cache[i].t;
+            }
+    }
+    return p->tuning;
+}
+
+void cache_tuning(frnn_plan* p, const TuneKey& key, const frnn_tuning& t)
+{
+    for (int i = 0; i < p->n_tune; ++i)
+        if (p->tune_cache[i].key == key) {
+            p->tune_cache[i].t = t;
+            return;
+        }
+    const int i = p->n_tune < kTuneCache ? p->n_tune++ : (p->tune_next++ % kTuneCache);
+    p->tune_cache[i].key = key;
+    p->tune_cache[i].t = t;
+}
 
 template <typename T>
 int plan_alloc(frnn_plan* p, T** out, long long count)
@@ -114,7 +180,6 @@ void plan_free_all(frnn_plan* p)
     }
     for (int i = 0; i < p->n_allocs; ++i) cudaFree(p->allocs[i]);
     p->n_allocs = 0;
-    if (p->d_input) cudaFree(p->d_input);
 }
 
 // Restore every buffer that must be zero (or +-inf encoded) between builds.
@@ -153,12 +218,12 @@ int get_walk_cfg(frnn_plan* p, int dp4, int cap, LaunchCfg* out)
     return FRNN_OK;
 }
 
-int launch(frnn_plan* p, int dp4, int cap, cudaStream_t s, cudaEvent_t* stage_ev)
+int launch(frnn_plan* p, int dp4, int cap, int walk_tuning, cudaStream_t s, cudaEvent_t* stage_ev)
 {
     LaunchCfg cfg;
     int rc = get_walk_cfg(p, dp4, cap, &cfg);
     if (rc != FRNN_OK) return rc;
-    const int walk = resolve_walk(p->tuning.walk, dp4);
+    const int walk = resolve_walk(walk_tuning, dp4);
     if (stage_ev || !(p->prm.flags & FRNN_USE_GRAPH))
         return launch_build(p->st, dp4, cfg, walk, s, stage_ev) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
     GraphEntry* ge = nullptr;
@@ -224,12 +289,25 @@ int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off
     return FRNN_OK;
 }
 
+int autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, float r, int k,
+             cudaStream_t s, frnn_tuning* best, float* best_ms);
+
+// One radius build, or with probe_out set the autotuner's probe of the grid
+// (stages 1-3 and the candidate count; the outputs are not written).
 int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d,
-                  float r, int k, cudaStream_t s, frnn_csr* out, cudaEvent_t* stage_ev = nullptr)
+                  float r, int k, cudaStream_t s, frnn_csr* out, cudaEvent_t* stage_ev = nullptr,
+                  unsigned long long* probe_out = nullptr)
 {
     long long n_total = 0;
     int rc = check_build_args(p, emb, ev_off, n_events, d, r, k, out, &n_total);
     if (rc != FRNN_OK) return rc;
+    bool cached = false;
+    frnn_tuning tu = tuning_for(p, ev_off, n_events, d, r, k, &cached);
+    if (!cached && !p->tuning_fixed && (p->prm.flags & FRNN_AUTOTUNE) && n_total > 0 && !probe_out) {
+        // first call of this shape: tune it (synchronous, off the steady-state path)
+        rc = autotune(p, emb, ev_off, n_events, d, r, k, s, &tu, nullptr);
+        if (rc != FRNN_OK) return rc;
+    }
     const DevState& st = p->st;
     out->row_ptr = st.row_ptr;
     out->col = st.col;
@@ -278,8 +356,8 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->k = (k == FRNN_NO_CAP) ? 0x7fffffff : k;
     h->r = r;
     h->r2 = r * r;
-    h->g_max = p->tuning.g_max;
-    h->cell_scale = p->tuning.cell_scale;
+    h->g_max = tu.g_max;
+    h->cell_scale = tu.cell_scale;
     h->emit_d2 = (p->prm.flags & FRNN_EMIT_D2) ? 1 : 0;
     h->knn = 0;
     h->stall = p->stall_next ? 1 : 0;
@@ -289,8 +367,12 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;
     if (cudaEventRecord(p->ring_ev[slot], s) != cudaSuccess) return FRNN_ERR_CUDA;
+    if (probe_out) {
+        p->has_last = false;  // a probe leaves no graph behind
+        return launch_probe(p->st, p->base_cfg, probe_out, s) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
+    }
     const int cap = next_pow2((k > 32 ? k : 32) + 32);
-    rc = launch(p, h->dp / 4, cap, s, stage_ev);
+    rc = launch(p, h->dp / 4, cap, tu.walk, s, stage_ev);
     if (rc != FRNN_OK) return rc;
     p->last = *out;
     p->last_r2 = r * r;
@@ -335,7 +417,109 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     b += sizeof(unsigned long long) * (tiles_c + tiles_r);
     b += sizeof(int) * ec * 2 + (d2 ? 2 * sizeof(float) * ec : 0);
     b += 8 + sizeof(int) * (ev + 1) + 4;
+    b += 3 * sizeof(unsigned long long);  // autotuner probe
+    b += sizeof(float) * n * (unsigned long long)q.d_max;  // input of the host-to-host call
     return b;
+}
+
+// The autotuner (the choice of gridded dimensions that the paper makes by
+// hand, Sec. 3.4, plus the form of the walk).  Every grid of the search
+// (g_max x cell_scale) is first probed: stages 1-3 and a count of the exact
+// candidate tests, non-empty cells and cell slots the walk and the scans
+// would handle.  A cost in candidate-test units, tests + 20 x non-empty cells
+// (a segment's set-up) + 2 x cell slots (the scans), keeps the three cheapest
+// grids; those are timed with each walk form (best of three builds after a
+// warm-up) and the fastest is set on the plan and cached for the call's shape.
+int autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, float r, int k,
+             cudaStream_t s, frnn_tuning* best, float* best_ms)
+{
+    static const int kG[] = {6, 5, 4, 3, 2};
+    static const float kScale[] = {1.0f, 1.25f, 1.5f, 2.0f};
+    constexpr int kGrids = 20, kFinalists = 3;
+    frnn_csr out;
+    long long n_total = 0;
+    int rc = check_build_args(p, emb, ev_off, n_events, d, r, k, &out, &n_total);
+    if (rc != FRNN_OK) return rc;
+    const frnn_tuning saved = p->tuning;
+    if (n_total == 0) {
+        if (best) *best = saved;
+        if (best_ms) *best_ms = 0.f;
+        return FRNN_OK;
+    }
+    p->tuning_fixed = true;
+    // probe every grid
+    struct Cand {
+        frnn_tuning t;
+        double cost;
+    };
+    Cand cand[kGrids];
+    unsigned long long h_probe[3];
+    for (int i = 0; i < kGrids && rc == FRNN_OK; ++i) {
+        p->tuning.g_max = kG[i / 4];
+        p->tuning.cell_scale = kScale[i % 4];
+        p->tuning.walk = kWalkAuto;
+        rc = build_batched(p, emb, ev_off, n_events, d, r, k, s, &out, nullptr, p->probe);
+        if (rc != FRNN_OK) break;
+        if (cudaMemcpyAsync(h_probe, p->probe, sizeof(h_probe), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            rc = FRNN_ERR_CUDA;
+            break;
+        }
+        unsigned bits = 0;
+        rc = read_status_bits(p, s, &bits);  // synchronises the stream
+        if (rc == FRNN_OK && (bits & kStTimeout)) rc = FRNN_ERR_TIMEOUT;
+        cand[i].t = p->tuning;
+        cand[i].cost = (double)h_probe[0] + 20.0 * (double)h_probe[1] + 2.0 * (double)h_probe[2];
+    }
+    // time the cheapest grids with each walk form
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == FRNN_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = FRNN_ERR_CUDA;
+    }
+    frnn_tuning win = saved;
+    float win_ms = -1.f;
+    if (rc == FRNN_OK) {
+        std::sort(cand, cand + kGrids, [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
+        const int dp4 = (d + 3) / 4;
+        const int n_walks = dp4 <= kMaxDp4QueryMajor ? 2 : 1;
+        for (int f = 0; f < kFinalists && rc == FRNN_OK; ++f) {
+            for (int w = 0; w < n_walks && rc == FRNN_OK; ++w) {
+                p->tuning = cand[f].t;
+                p->tuning.walk = w == 0 ? kWalkCandMajor : kWalkQueryMajor;
+                rc = build_batched(p, emb, ev_off, n_events, d, r, k, s, &out);  // warm-up (and graph capture)
+                float best_rep = -1.f;
+                for (int rep = 0; rep < 3 && rc == FRNN_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    rc = build_batched(p, emb, ev_off, n_events, d, r, k, s, &out);
+                    cudaEventRecord(e1, s);
+                    if (rc != FRNN_OK) break;
+                    float ms = 0.f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = FRNN_ERR_CUDA;
+                        break;
+                    }
+                    if (best_rep < 0.f || ms < best_rep) best_rep = ms;
+                }
+                if (rc != FRNN_OK) break;
+                unsigned bits = 0;
+                rc = read_status_bits(p, s, &bits);
+                if (rc == FRNN_OK && (bits & kStTimeout)) rc = FRNN_ERR_TIMEOUT;
+                if (rc == FRNN_OK && (win_ms < 0.f || best_rep < win_ms)) {
+                    win_ms = best_rep;
+                    win = p->tuning;
+                }
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    p->tuning_fixed = false;
+    p->tuning = (rc == FRNN_OK && win_ms >= 0.f) ? win : saved;
+    if (rc == FRNN_OK && win_ms < 0.f) rc = FRNN_ERR_CUDA;
+    if (rc == FRNN_OK) cache_tuning(p, tune_key(ev_off, n_events, d, r, k), win);
+    if (best) *best = p->tuning;
+    if (best_ms) *best_ms = win_ms;
+    return rc;
 }
 
 }  // namespace
@@ -430,6 +614,9 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.pool_ctr, 1);
     ALLOC(st.edge_off, ev + 1);
     ALLOC(st.status, 1);
+    ALLOC(p->probe, 3);
+    ALLOC(p->d_input, n * q.d_max);  // the device copy of frnn_build_graph_host's input
+    p->d_input_floats = n * q.d_max;
 #undef ALLOC
     for (int i = 0; rc == FRNN_OK && i < kRing; ++i) {
         if (cudaHostAlloc(reinterpret_cast<void**>(&p->h_call[i]), p->call_bytes, cudaHostAllocDefault) != cudaSuccess ||
@@ -474,6 +661,8 @@ int frnn_plan_set_tuning(frnn_plan* p, const frnn_tuning* t)
     p->tuning.g_max = g;
     p->tuning.cell_scale = cs;
     p->tuning.walk = t->walk;
+    p->n_tune = 0;  // an explicit tuning replaces every autotuned one
+    p->tune_next = 0;
     return FRNN_OK;
 }
 
@@ -626,54 +815,17 @@ int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, in
     if (!p) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    static const int kG[] = {6, 5, 4, 3, 2};
-    static const float kScale[] = {1.0f, 1.25f, 1.5f, 2.0f};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        cudaGetLastError();
-        return FRNN_ERR_CUDA;
-    }
-    const frnn_tuning saved = p->tuning;
-    frnn_tuning win = saved;
-    float win_ms = -1.f;
-    int rc = FRNN_OK;
-    frnn_csr out;
-    for (int gi = 0; gi < 5 && rc == FRNN_OK; ++gi) {
-        for (int si = 0; si < 4 && rc == FRNN_OK; ++si) {
-            p->tuning.g_max = kG[gi];
-            p->tuning.cell_scale = kScale[si];
-            rc = build_batched(p, emb, ev_off, n_events, d, r, k_max, s, &out);  // warm-up (and graph capture)
-            if (rc != FRNN_OK) break;
-            float best_rep = -1.f;
-            for (int rep = 0; rep < 3 && rc == FRNN_OK; ++rep) {
-                cudaEventRecord(e0, s);
-                rc = build_batched(p, emb, ev_off, n_events, d, r, k_max, s, &out);
-                cudaEventRecord(e1, s);
-                if (rc != FRNN_OK) break;
-                float ms = 0.f;
-                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    rc = FRNN_ERR_CUDA;
-                    break;
-                }
-                if (best_rep < 0.f || ms < best_rep) best_rep = ms;
-            }
-            if (rc != FRNN_OK) break;
-            const int st = frnn_get_last_status(p, stream);
-            if (st == FRNN_OK && (win_ms < 0.f || best_rep < win_ms)) {
-                win_ms = best_rep;
-                win = p->tuning;
-            }
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->tuning = (rc == FRNN_OK && win_ms >= 0.f) ? win : saved;
-    if (rc == FRNN_OK && win_ms < 0.f) rc = FRNN_ERR_CUDA;
-    if (best) *best = p->tuning;
-    if (best_ms) *best_ms = win_ms;
-    return rc;
+    return autotune(p, emb, ev_off, n_events, d, r, k_max, static_cast<cudaStream_t>(stream), best, best_ms);
+}
+
+int frnn_plan_tuning_for(const frnn_plan* p, const int64_t* ev_off, int n_events, int d, float r, int k_max,
+                         frnn_tuning* out, int* cached)
+{
+    if (!p || !ev_off || !out || n_events < 1) return FRNN_ERR_INVALID_ARG;
+    bool c = false;
+    *out = tuning_for(p, ev_off, n_events, d, r, k_max, &c);
+    if (cached) *cached = c ? 1 : 0;
+    return FRNN_OK;
 }
 
 int frnn_label_components(frnn_plan* p, float d2_max, void* stream, int32_t* labels)
@@ -732,20 +884,7 @@ int frnn_build_graph_host(frnn_plan* p, const float* h_emb, const int64_t* ev_of
     if (n < 0 || (n > 0 && !h_emb) || d < 1 || d > kMaxDims) return FRNN_ERR_INVALID_ARG;
     if (n > p->prm.n_max || d > p->prm.d_max) return FRNN_ERR_CAPACITY;
     const long long need = n * d;
-    if (need > p->d_input_floats) {
-        if (p->d_input) {
-            cudaStreamSynchronize(s);
-            cudaFree(p->d_input);
-            p->d_input = nullptr;
-            p->d_input_floats = 0;
-        }
-        const long long want = p->prm.n_max * (long long)p->prm.d_max;
-        if (cudaMalloc(reinterpret_cast<void**>(&p->d_input), sizeof(float) * (size_t)(want > 0 ? want : 1)) != cudaSuccess) {
-            cudaGetLastError();
-            return FRNN_ERR_OOM;
-        }
-        p->d_input_floats = want;
-    }
+    if (need > p->d_input_floats) return FRNN_ERR_CAPACITY;  // cannot happen: sized at creation for n_max x d_max
     if (n > 0 && cudaMemcpyAsync(p->d_input, h_emb, sizeof(float) * (size_t)need, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;
     frnn_csr csr;

@@ -160,6 +160,11 @@ int launch_label(const DevState& st, int* parent, int* labels, float d2_max, int
 int launch_edge_features(const DevState& st, const float* emb, int d, long long e_begin, long long e_end,
                          float* out, int n_sm, void* stream);
 int config_pt(int n_sm, LaunchCfg* cfg);
+// Autotuner probe: stages 1-3 of a radius build on the current tuning, then
+// out[0] = candidate tests a collect walk would make, out[1] = non-empty
+// cells, out[2] = cell slots scanned (device, 3 x u64).  Leaves the plan's
+// between-builds state as a build does.
+int launch_probe(const DevState& st, const LaunchCfg& cfg, unsigned long long* out, void* stream);
 // The k-nearest-neighbour build (no radius): grid, fixed-length rows, ring walk.
 int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream);
 

@@ -1665,6 +1665,63 @@ __device__ __forceinline__ bool append_runs(const WarpWalk& ww, const int2* run_
     return true;
 }
 
+// Runs of up to kSegGroup consecutive segments of one event with at most 4
+// gridded dims (27 runs each, one per lane): every segment's cell-table loads
+// are issued before any is used, then the non-empty runs are appended to the
+// run list segment by segment, stopping at the first that does not fit.
+// segs: the segments to list (bits of their first lanes, all of this event);
+// cs: the lane's cell id.  Returns the bits of the segments listed.
+constexpr int kSegGroup = 8;
+
+__device__ __forceinline__ unsigned list_runs_g4(const WarpWalk& ww, const int2* run_tab, const int* cell_start,
+                                                 unsigned segs, unsigned cs, int lane, int2* runs, int2* segb,
+                                                 int& cnt)
+{
+    const EvPlan& pl = ww.pl;
+    const int g = pl.g;
+    const int nr = n_runs(g);
+    const int ncl = pl.ncell[g - 1];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // run ri = lane: cell offset along the slower dims, and the faces it crosses
+    const int2 rt = lane < nr ? __ldg(run_tab + lane) : make_int2(0, 0);
+    int a[kSegGroup], lo[kSegGroup], hi[kSegGroup];
+    unsigned rem = segs;
+#pragma unroll
+    for (int u = 0; u < kSegGroup; ++u) {
+        a[u] = rem ? __ffs(rem) - 1 : -1;
+        rem &= rem - 1;
+        lo[u] = 0;
+        hi[u] = 0;
+        if (a[u] >= 0) {
+            const unsigned c = __shfl_sync(kFull, cs, a[u]);
+            // the segment's cell coordinates (lane t: dim t) and the grid faces it lies on
+            const int kt = lane < g ? (int)((c / (unsigned)pl.stride[lane]) % (unsigned)pl.ncell[lane]) : 0;
+            unsigned face = 0;
+            if (lane < g - 1) face = (kt == 0 ? 1u << lane : 0u) | (kt == pl.ncell[lane] - 1 ? 1u << (5 + lane) : 0u);
+            const unsigned bad = __reduce_or_sync(kFull, face);
+            const int kl = __shfl_sync(kFull, kt, g - 1);
+            if (lane < nr && (rt.y & (int)bad) == 0) {
+                const int base = pl.cell_off + (int)c + rt.x - kl;
+                lo[u] = __ldg(cell_start + base + max(kl - 1, 0));
+                hi[u] = __ldg(cell_start + base + min(kl + 1, ncl - 1) + 1);
+            }
+        }
+    }
+    unsigned listed = 0;
+#pragma unroll
+    for (int u = 0; u < kSegGroup; ++u) {
+        if (a[u] < 0) break;
+        const bool ne = hi[u] > lo[u];
+        const unsigned m = __ballot_sync(kFull, ne);
+        if (cnt + __popc(m) > kRunCap) break;
+        if (ne) runs[cnt + __popc(m & lt_mask)] = make_int2(lo[u], hi[u]);
+        if (lane == 0) segb[a[u]] = make_int2(cnt, cnt + __popc(m));
+        cnt += __popc(m);
+        listed |= 1u << a[u];
+    }
+    return listed;
+}
+
 // d2 of a query against a candidate row, both as pairs of dims (a float4 is
 // two pairs): each pair is subtracted and squared as one packed operation
 // (two IEEE single operations), and the squares are added one at a time in
@@ -1685,6 +1742,22 @@ __device__ __forceinline__ float dist2_rows(const ulonglong2 (&qv)[DP4], const u
     return s;
 }
 
+// Candidate row at sorted position pos, as pairs of dims (32-byte loads when
+// a row is 8 floats: rows are then 32-byte aligned).
+template <int DP4>
+__device__ __forceinline__ void load_row(const ulonglong2* xs2, int pos, ulonglong2 (&cv)[DP4])
+{
+    const ulonglong2* p = xs2 + (long long)pos * DP4;
+    if constexpr (DP4 == 2) {
+        asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(cv[0].x), "=l"(cv[0].y), "=l"(cv[1].x), "=l"(cv[1].y)
+            : "l"(p));
+    } else {
+#pragma unroll
+        for (int k = 0; k < DP4; ++k) cv[k] = __ldg(p + k);
+    }
+}
+
 template <int DP4>
 __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
 {
@@ -1695,7 +1768,7 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
     unsigned long long* keys = s_qwords + (size_t)wib * kQWarpWords;
     int2* runs = reinterpret_cast<int2*>(keys + 32 * kRowStride);
     int2* segb = runs + kRunCap;  // per segment (indexed by its first lane): its entries of the run list
-    unsigned long long* my_row = keys + lane * kRowStride;
+    uint2* my_row2 = reinterpret_cast<uint2*>(keys + lane * kRowStride);  // keys as {low word, high word}
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
     const int B = st.hdr->n_events;
@@ -1738,68 +1811,82 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
                 while (todo) {
                     const int a = __ffs(todo) - 1;
                     const int sb = __shfl_sync(kFull, le.b, a);
-                    const unsigned csa = __shfl_sync(kFull, cs, a);
                     if (sb != plan_b) {
                         load_plan(ww, st.plan, sb, lane);
                         plan_b = sb;
                     }
-                    const int lo_r = cnt;
-                    if (!ww.pl.skip) {
+                    // the following segments of the same event
+                    const unsigned same = todo & __ballot_sync(kFull, le.b == sb);
+                    const int2* run_tab = st.run_tab + (size_t)sb * kMaxRuns;
+                    unsigned listed;
+                    if (ww.pl.skip) {
+                        // an event holding NaN or Inf: its rows stay empty
+                        if (lane == 0)
+                            for (unsigned m = same; m; m &= m - 1) segb[__ffs(m) - 1] = make_int2(cnt, cnt);
+                        listed = same;
+                    } else if (ww.pl.g <= 4) {
+                        unsigned grp = same;
+                        for (int u = kSegGroup; u > 0 && grp; --u) grp &= grp - 1;
+                        grp = same & ~grp;  // its first kSegGroup segments
+                        listed = list_runs_g4(ww, run_tab, st.cell_start, grp, cs, lane, runs, segb, cnt);
+                        if (listed != grp) {  // the list is full
+                            batch |= listed;
+                            todo &= ~listed;
+                            break;
+                        }
+                    } else {
                         // the segment's cell coordinates, from its cell id
+                        const unsigned csa = __shfl_sync(kFull, cs, a);
                         if (lane < ww.pl.g)
                             ww.ks[lane] = (int)((csa / (unsigned)ww.pl.stride[lane]) % (unsigned)ww.pl.ncell[lane]);
                         __syncwarp();
-                        if (!append_runs(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, runs, cnt))
-                            break;
+                        const int lo_r = cnt;
+                        if (!append_runs(ww, run_tab, st.cell_start, lane, runs, cnt)) break;
+                        if (lane == 0) segb[a] = make_int2(lo_r, cnt);
+                        listed = 1u << a;
                     }
-                    if (lane == 0) segb[a] = make_int2(lo_r, cnt);
-                    batch |= 1u << a;
-                    todo &= todo - 1;
+                    batch |= listed;
+                    todo &= ~listed;
                 }
                 __syncwarp();
-                // every lane of the batch streams its segment's candidates
-                int li = 0, hi = 0, pos = 0, end = 0;
+                // every lane of the batch streams its segment's candidates, two
+                // per step.  The step is branch-free: a lane with no work left
+                // (or none in this batch) runs it on a valid row with its hits
+                // masked, and a lane at the end of a run takes the next one by
+                // selection.  A key is stored as the pair {position, d2 bits},
+                // i.e. the 64-bit value (d2 bits << 32) | position.
+                int li = 0, hi = 0;
                 if (valid && ((batch >> my_a) & 1u)) {
                     const int2 sbd = segb[my_a];
                     li = sbd.x;
                     hi = sbd.y;
                 }
                 bool act = li < hi;
-                if (act) {
-                    const int2 rr = runs[li];
-                    pos = rr.x;
-                    end = rr.y;
-                }
+                const int2 r0 = runs[act ? li : 0];
+                int pos = act ? r0.x : 0, end = act ? r0.y : 1;
                 while (__any_sync(kFull, act)) {
-                    if (act) {
-                        const bool two = pos + 1 < end;
-                        const ulonglong2* ra = xs2 + (long long)pos * DP4;
-                        const ulonglong2* rb = two ? ra + DP4 : ra;
-                        ulonglong2 ca[DP4], cb[DP4];
-#pragma unroll
-                        for (int k = 0; k < DP4; ++k) ca[k] = __ldg(ra + k);
-#pragma unroll
-                        for (int k = 0; k < DP4; ++k) cb[k] = __ldg(rb + k);
-                        const float da = dist2_rows<DP4>(qv, ca);
-                        const float db = dist2_rows<DP4>(qv, cb);
-                        if (da <= r2) {
-                            if (deg < kRowSlots) my_row[deg] = edge_key(da, pos);
-                            ++deg;
-                        }
-                        if (two && db <= r2) {
-                            if (deg < kRowSlots) my_row[deg] = edge_key(db, pos + 1);
-                            ++deg;
-                        }
-                        pos += 2;
-                        if (pos >= end) {
-                            if (++li < hi) {
-                                const int2 rr = runs[li];
-                                pos = rr.x;
-                                end = rr.y;
-                            } else {
-                                act = false;
-                            }
-                        }
+                    const int pb = min(pos + 1, end - 1);  // the run's last point twice when it is odd
+                    ulonglong2 ca[DP4], cb[DP4];
+                    load_row<DP4>(xs2, pos, ca);
+                    load_row<DP4>(xs2, pb, cb);
+                    const float da = dist2_rows<DP4>(qv, ca);
+                    const float db = dist2_rows<DP4>(qv, cb);
+                    const bool ha = act && da <= r2;
+                    const bool hb = act && pb > pos && db <= r2;
+                    if (ha && deg < kRowSlots) my_row2[deg] = make_uint2((unsigned)pos, __float_as_uint(da));
+                    deg += ha;
+                    if (hb && deg < kRowSlots) my_row2[deg] = make_uint2((unsigned)pb, __float_as_uint(db));
+                    deg += hb;
+                    pos += 2;
+                    const bool adv = pos >= end;
+                    li += adv;
+                    const int2 rn = runs[min(li, kRunCap - 1)];
+                    act = act && li < hi;
+                    pos = adv ? rn.x : pos;
+                    end = adv ? rn.y : end;
+                    if (!act) {
+                        pos = 0;
+                        end = 1;
                     }
                 }
                 __syncwarp();  // the run list is rewritten for the next batch
@@ -2245,6 +2332,68 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_knn(Dev
     }
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner probe (Sec. 3.4: the cost of the cell walk grows with the cells
+// a point's neighbourhood spans).  After stages 1-3 on a candidate grid, the
+// exact work of a collect walk on it: out[0] += sum over non-empty cells c of
+// n_c x (points in the runs of cells around c), the candidate tests; out[1]
+// += the non-empty cells (about one segment each); out[2] = the cell slots
+// the scans cover.  One thread per cell slot.
+__global__ void __launch_bounds__(kPtThreads) k_cell_cost(DevState st, unsigned long long* out)
+{
+    const int B = st.hdr->n_events;
+    const long long C = *st.cells_total;
+    unsigned long long cand = 0, cells = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (long long)gridDim.x * blockDim.x) {
+        const int n_c = __ldg(st.cell_start + c + 1) - __ldg(st.cell_start + c);
+        if (n_c == 0) continue;
+        // the cell's event: the last event whose table starts at or before c
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&st.plan[mid].cell_off) <= c) lo = mid; else hi = mid - 1;
+        }
+        const EvPlan& pl = st.plan[lo];
+        const int local = (int)(c - pl.cell_off);
+        int kc[kMaxG];
+#pragma unroll
+        for (int t = 0; t < kMaxG; ++t) kc[t] = (t < pl.g) ? (local / pl.stride[t]) % pl.ncell[t] : 0;
+        const int g = pl.g;
+        const int nr = n_runs(g);
+        const int kl = kc[g - 1], ncl = pl.ncell[g - 1];
+        long long sum = 0;
+        for (int ri = 0; ri < nr; ++ri) {
+            int rem = ri, cb = 0;
+            bool ok = true;
+#pragma unroll
+            for (int t = 0; t < kMaxG - 1; ++t) {
+                if (t < g - 1) {
+                    const int kt = kc[t] + (rem % 3) - 1;
+                    rem /= 3;
+                    ok &= (kt >= 0) && (kt < pl.ncell[t]);
+                    cb += kt * pl.stride[t];
+                }
+            }
+            if (!ok) continue;
+            const int c0 = pl.cell_off + cb + max(kl - 1, 0);
+            const int c1 = pl.cell_off + cb + min(kl + 1, ncl - 1);
+            sum += __ldg(st.cell_start + c1 + 1) - __ldg(st.cell_start + c0);
+        }
+        cand += (unsigned long long)n_c * (unsigned long long)sum;
+        cells += 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_xor_sync(kFull, cand, o);
+        cells += __shfl_xor_sync(kFull, cells, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cand) atomicAdd(out, cand);
+        if (cells) atomicAdd(out + 1, cells);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[2] = (unsigned long long)C;
+}
+
 // Stage boundaries: ev[i] is recorded before stage i and ev[7] after the last
 // (all NULL for an untimed build).
 inline void mark(cudaEvent_t* ev, int i, cudaStream_t s)
@@ -2374,6 +2523,18 @@ int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream)
 #undef FRNN_CASE
         default: return (int)cudaErrorInvalidValue;
     }
+}
+
+int launch_probe(const DevState& st, const LaunchCfg& cfg, unsigned long long* out, void* stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return (int)e;
+    k_bbox_plan<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_key_hist<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
+    k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
+    k_cell_cost<<<cfg.grid_pt, kPtThreads, 0, s>>>(st, out);
+    return (int)cudaGetLastError();
 }
 
 int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg)

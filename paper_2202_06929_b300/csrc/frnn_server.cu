@@ -277,10 +277,10 @@ void on_built(frnn_server* srv, Slot& s)
             // rows are written for every request whose edges end within the
             // slot's capacity (with an overflow, a prefix of the batch)
             while (s.n_ok < nb && (int64_t)s.h_edge_off[s.n_ok + 1] <= s.cap_edges) ++s.n_ok;
+            // every complete request's columns come to the host (also for a
+            // trace replay, whose requests keep no copy of their own)
             const int64_t e_ok = s.h_edge_off[s.n_ok];
-            bool any_keep = false;
-            for (int i = 0; i < s.n_ok; ++i) any_keep |= s.reqs[(size_t)i]->keep;
-            if (any_keep && e_ok > 0)
+            if (e_ok > 0)
                 cudaMemcpyAsync(s.h_col, s.csr.col, sizeof(int32_t) * (size_t)e_ok, cudaMemcpyDeviceToHost,
                                 s.stream);
         }

@@ -100,15 +100,47 @@ def test_pileup_scale_event(name):
 
 
 def test_autotune_keeps_result():
+    """The autotuner (probe every grid, time the cheapest with both walk
+    forms) may change speed, never the result; its choice is cached for the
+    call's shape and an explicit tuning drops the cache."""
     evs = [synth.make_event("c2", e, n=30_000) for e in range(4)]
     off = np.concatenate([[0], np.cumsum([e.shape[0] for e in evs])]).astype(np.int64)
     xt = torch.from_numpy(np.concatenate(evs)).cuda()
     with frnn.Plan(n_max=int(off[-1]), d_max=8, k_max_cap=256, events_max=4, cells_per_point=32) as plan:
         ref = plan.build_batched(xt, off, 0.1, 256).to_host()
+        assert plan.tuning_for(off, 8, 0.1, 256)[3] is False
         g, scale, ms = plan.autotune(xt, off, 0.1, 256)
         assert g in (2, 3, 4, 5, 6) and scale in (1.0, 1.25, 1.5, 2.0) and ms > 0
-        assert plan.get_tuning()[:2] == (g, scale)
+        g2, s2, walk, cached = plan.tuning_for(off, 8, 0.1, 256)
+        assert (g2, s2) == (g, scale) and walk in (1, 2) and cached
+        assert plan.get_tuning() == (g2, s2, walk)
+        # another shape (one event) is not covered by the entry
+        assert plan.tuning_for(off[:2], 8, 0.1, 256)[3] is False
         got = plan.build_batched(xt, off, 0.1, 256).to_host()
         assert plan.last_status() == 0
+        plan.set_tuning(3, 1.5, 1)
+        assert plan.tuning_for(off, 8, 0.1, 256) == (3, 1.5, 1, False)
     np.testing.assert_array_equal(got["row_ptr"], ref["row_ptr"])
     np.testing.assert_array_equal(got["col"], ref["col"])
+
+
+def test_autotune_flag_tunes_each_new_shape():
+    """FRNN_AUTOTUNE: the first build of a call shape autotunes it; the rows
+    equal the oracle's for each shape."""
+    evs = [synth.make_event("c3", e, n=20_000) for e in range(3)]
+    w = synth.WORKLOADS["c3"]
+    with frnn.Plan(n_max=60_000, d_max=8, k_max_cap=64, events_max=3, cells_per_point=32, autotune=True,
+                   use_graph=True) as plan:
+        for sel in ([0], [0, 1, 2]):
+            x = np.concatenate([evs[i] for i in sel])
+            off = np.concatenate([[0], np.cumsum([evs[i].shape[0] for i in sel])]).astype(np.int64)
+            assert plan.tuning_for(off, 8, w.r, w.k)[3] is False
+            csr = plan.build_batched(torch.from_numpy(x).cuda(), off, w.r, w.k)
+            host = csr.to_host()
+            assert plan.last_status() == 0
+            assert plan.tuning_for(off, 8, w.r, w.k)[3] is True
+            for b, i in enumerate(sel):
+                rp, col = csr.event_rows(host, b)
+                orp, ocol = oracle.radius_graph(evs[i], w.r, w.k)
+                np.testing.assert_array_equal(rp, orp)
+                np.testing.assert_array_equal(col, ocol)
