@@ -307,23 +307,26 @@ def measured_collect(stage: str, workload: str, walk: int):
     return m if sha.startswith(m["source_sha1_prefix"]) else None
 
 
-def stage_bytes(n_total: int, n_edges: int, d: int):
+def stage_bytes(n_total: int, n_edges: int, d: int, long_edges: int = 0, long_rows: int = 0):
     """Algorithmic bytes of each stage for a batch (each stage's unavoidable
-    reads of its inputs and writes of its outputs, counted once)."""
+    reads of its inputs and writes of its outputs, counted once).  long_edges
+    / long_rows: the edges and rows of the rows longer than the collect walk
+    parks (the emit walk writes those)."""
     dp = (d + 3) // 4 * 4
+    parked = n_edges - long_edges
     return {
         "bbox_plan": 4 * n_total * d,
         "key_hist": 4 * n_total * d + 8 * n_total,
         "scan_cells": 0,  # size of the cell table, reported separately
         "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total,
         # sorted points read once; per point its cell id, count and pool slot; rows parked
-        "walk_collect": 4 * n_total * dp + 4 * n_total + 8 * n_total + 4 * n_edges,
+        "walk_collect": 4 * n_total * dp + 4 * n_total + 8 * n_total + 4 * parked,
         # per point its count and pool slot read, row_ptr written; parked rows
         # read from the pool and written to col
-        "scan_rows": 12 * n_total + 8 * n_edges,
-        # only the rows longer than the collect walk keeps (none on the C2
-        # workload): not counted
-        "walk_emit": 0,
+        "scan_rows": 12 * n_total + 8 * parked,
+        # the long rows: per row its list entry, count and offset read, its
+        # columns written
+        "walk_emit": 12 * long_rows + 4 * long_edges,
     }
 
 
@@ -715,7 +718,10 @@ def main(argv=None):
                 stage_ms[s].append(ms[s])
     stage_avg = {s: float(np.mean(v[1:])) for s, v in stage_ms.items()}
     dom = max(stage_avg, key=stage_avg.get)
-    sbytes = stage_bytes(n_total, n_edges, d)
+    row_len = np.diff(plan.build_batched(x_dev, off, r, k, stream=stream).to_host()["row_ptr"].astype(np.int64))
+    torch.cuda.synchronize(dev)
+    long_mask = row_len > KFAST_ROWS
+    sbytes = stage_bytes(n_total, n_edges, d, int(row_len[long_mask].sum()), int(long_mask.sum()))
     hbm_peak, peak_kind = measured_peaks()
     # the build's algorithmic bytes (read the points once, write the CSR once)
     whole_bytes = 4 * n_total * d + 4 * (n_total + 1) + 4 * n_edges
@@ -795,9 +801,7 @@ def main(argv=None):
     if rank == 0:
         g_used, s_used, _ = plan.get_tuning()
         mean_cand, g_grid = host_candidates(x_host[off[0]:off[1]], r, g_used, s_used, cpp)
-        row_len = np.diff(plan.build_batched(x_dev, off, r, k, stream=stream).to_host()["row_ptr"].astype(np.int64))
-        torch.cuda.synchronize(dev)
-        long_frac = float(np.mean(row_len > KFAST_ROWS))
+        long_frac = float(np.mean(long_mask))
         evals = mean_cand * n_total * (1.0 + long_frac)
         ops = evals * 3 * d
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count

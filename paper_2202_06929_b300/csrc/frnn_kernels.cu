@@ -1484,6 +1484,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
                 const unsigned long long kk = row[e - xin];
                 if (kk != self_key) {
                     int rank = (self_key < kk) ? -1 : 0;
+#pragma unroll 4
                     for (int y = 0; y < nl; ++y) rank += row[y] < kk;
                     if (rank < cl) {
                         st.pool[base_off + ol + rank] = (int)(unsigned)kk;
@@ -1514,6 +1515,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
+    const int kStop = max(st.hdr->k, kRowSlots);  // hits past which a row is long and capped
     const int B = st.hdr->n_events;
     const long long nchunks = (P + 31) >> 5;
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
@@ -1557,8 +1559,13 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                 if (ww.pl.skip) continue;
                 segment_cell(ww, sq + (a >> 1) * (2 * DP), a & 1, lane);
                 const int p0 = a >> 1, p1 = (e + 1) >> 1;  // query pairs covering [a, e)
+                // a query with more than max(k, kRowSlots) hits (itself included)
+                // has its final count, min(|S_i|, k) = k, and its row goes to the
+                // emit walk, which walks every candidate again: once every query
+                // of the segment is such a row, the segment's walk can stop
+                bool capped = false;
                 for_each_run_group(ww, st.run_tab + (size_t)sb * kMaxRuns, st.cell_start, lane, [&](const Runs& rn) {
-                    for (int base = 0; base < rn.total; base += 32) {
+                    for (int base = 0; base < rn.total && !capped; base += 32) {
                         const int cand = candidate_at(rn, base + lane);
                         CandPk<DP4> cp;
                         load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
@@ -1583,6 +1590,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                                 if (lane == i1) deg += __popc(m1);
                             }
                         }
+                        capped = __all_sync(kFull, lane < a || lane >= e || deg > kStop);
                     }
                 });
             }
@@ -1771,6 +1779,7 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
     uint2* my_row2 = reinterpret_cast<uint2*>(keys + lane * kRowStride);  // keys as {low word, high word}
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
+    const int kStop = max(st.hdr->k, kRowSlots);  // hits past which a row is long and capped
     const int B = st.hdr->n_events;
     const long long nchunks = (P + 31) >> 5;
     const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
@@ -1881,7 +1890,8 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
                     const bool adv = pos >= end;
                     li += adv;
                     const int2 rn = runs[min(li, kRunCap - 1)];
-                    act = act && li < hi;
+                    // past kStop hits the row is long (the emit walk takes it) and its count final
+                    act = act && li < hi && deg <= kStop;
                     pos = adv ? rn.x : pos;
                     end = adv ? rn.y : end;
                     if (!act) {
