@@ -578,10 +578,14 @@ def main(argv=None):
     epp = k if args.workload == "c5b" else 64  # edge slots per point (C5b rows hold up to K)
 
     cpp = 32  # cell slots per point: room for five or six gridded dims (the autotuner decides)
+    # the million-point workloads have rows longer than the walk parks: room
+    # to keep their neighbours (384 slots per row, 32 rows at a time)
+    hits = (lambda n: 32 * 384 * (n // 32 + B)) if args.workload in ("c5", "c5b") else (lambda n: 0)
     plan = frnn.Plan(n_max=n_total, d_max=d, k_max_cap=k, events_max=B, edge_capacity=n_total * epp,
-                     cells_per_point=cpp, use_graph=True, device=local)
+                     cells_per_point=cpp, use_graph=True, device=local, hit_capacity=hits(n_total))
     plan_one = frnn.Plan(n_max=n_max_event, d_max=d, k_max_cap=k, events_max=1,
-                         edge_capacity=n_max_event * epp, cells_per_point=cpp, use_graph=True, device=local)
+                         edge_capacity=n_max_event * epp, cells_per_point=cpp, use_graph=True, device=local,
+                         hit_capacity=hits(n_max_event))
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()
@@ -835,7 +839,7 @@ def main(argv=None):
                              + f" (seeded per event), D={d}, r={r}, K={k}, "
                                "one batched build per step replayed from a CUDA graph"),
                 "events_per_step": B, "n_per_event": N_PER_EVENT if args.workload == "c2" else None,
-                "d": d, "r": r, "k": k, "autotune": tuned,
+                "d": d, "r": r, "k": k, "autotune": tuned, "hit_capacity": hits(n_total),
                 "points_per_step": n_total, "edges_per_step": n_edges,
                 "l2": f"inputs larger than L2 ({x_host.nbytes / 1e6:.0f} MB of points per step, "
                       f"plus {4 * n_edges / 1e6:.0f} MB of col written)",

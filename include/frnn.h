@@ -81,6 +81,11 @@ typedef struct {
     int64_t edge_capacity; /* col slots; 0 = n_max * k_max_cap (never overflows)      */
     int cells_per_point;   /* cell-table slots per point (plus 4096 per event); 0 = 4 */
     uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH | FRNN_AUTOTUNE           */
+    int64_t hit_capacity;  /* 4-byte slots in which the neighbour walk keeps every
+                              neighbour of rows longer than 24 (384 per row, taken 32
+                              rows at a time), so that their k nearest are sorted from
+                              those instead of walking their candidates again (rows of
+                              up to 12 dims); 0 = none.  Speed only, never the result. */
 } frnn_plan_params;
 
 /*

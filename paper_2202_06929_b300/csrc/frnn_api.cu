@@ -194,6 +194,7 @@ int reset_device_state(frnn_plan* p, cudaStream_t s)
     ok &= cudaMemsetAsync(st.nonfinite, 0, sizeof(unsigned) * ev, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.counters, 0, sizeof(unsigned) * kCtrCount, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.pool_ctr, 0, sizeof(unsigned long long), s) == cudaSuccess;
+    if (st.spill_ctr) ok &= cudaMemsetAsync(st.spill_ctr, 0, sizeof(unsigned long long), s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.cell_count, 0, sizeof(unsigned) * p->cells_max, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.scan_cells, 0, sizeof(unsigned long long) * p->tiles_cells, s) == cudaSuccess;
     ok &= cudaMemsetAsync(st.scan_rows, 0, sizeof(unsigned long long) * p->tiles_rows, s) == cudaSuccess;
@@ -363,6 +364,12 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     h->stall = p->stall_next ? 1 : 0;
     p->stall_next = false;
     h->edge_capacity = p->edge_cap;
+    const int cap = next_pow2((k > 32 ? k : 32) + 32);
+    // long rows keep every hit when the plan has room: as many as the emit
+    // walk's two key buffers sort at once (rows of up to 16 floats)
+    h->spill_capacity = p->prm.hit_capacity;
+    h->spill_max = (p->prm.hit_capacity > 0 && h->dp / 4 <= 4) ? std::min(kSpillSlots, 2 * cap) : 0;
+    h->pad2 = 0;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;
@@ -371,7 +378,6 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
         p->has_last = false;  // a probe leaves no graph behind
         return launch_probe(p->st, p->base_cfg, probe_out, s) == 0 ? FRNN_OK : FRNN_ERR_CUDA;
     }
-    const int cap = next_pow2((k > 32 ? k : 32) + 32);
     rc = launch(p, h->dp / 4, cap, tu.walk, s, stage_ev);
     if (rc != FRNN_OK) return rc;
     p->last = *out;
@@ -386,7 +392,8 @@ int normalize_params(const frnn_plan_params* prm, frnn_plan_params* out, long lo
 {
     frnn_plan_params q = *prm;
     if (q.d_max < 1 || q.d_max > kMaxDims || q.n_max < 0 || q.events_max < 1 ||
-        q.k_max_cap < 1 || q.k_max_cap > 1024 || q.edge_capacity < 0 || q.cells_per_point < 0)
+        q.k_max_cap < 1 || q.k_max_cap > 1024 || q.edge_capacity < 0 || q.cells_per_point < 0 ||
+        q.hit_capacity < 0)
         return FRNN_ERR_INVALID_ARG;
     if (q.cells_per_point == 0) q.cells_per_point = 4;
     if (q.edge_capacity == 0) {
@@ -419,6 +426,8 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     b += 8 + sizeof(int) * (ev + 1) + 4;
     b += 3 * sizeof(unsigned long long);  // autotuner probe
     b += sizeof(float) * n * (unsigned long long)q.d_max;  // input of the host-to-host call
+    if (q.hit_capacity > 0)  // neighbours of long rows, and per long row its entry
+        b += sizeof(int) * (unsigned long long)q.hit_capacity + 8 + (sizeof(long long) + sizeof(int)) * n;
     return b;
 }
 
@@ -617,6 +626,12 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(p->probe, 3);
     ALLOC(p->d_input, n * q.d_max);  // the device copy of frnn_build_graph_host's input
     p->d_input_floats = n * q.d_max;
+    if (q.hit_capacity > 0) {
+        ALLOC(st.spill, q.hit_capacity);
+        ALLOC(st.spill_ctr, 1);
+        ALLOC(st.spill_at, n);
+        ALLOC(st.spill_n, n);
+    }
 #undef ALLOC
     for (int i = 0; rc == FRNN_OK && i < kRing; ++i) {
         if (cudaHostAlloc(reinterpret_cast<void**>(&p->h_call[i]), p->call_bytes, cudaHostAllocDefault) != cudaSuccess ||
@@ -769,6 +784,9 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     h->stall = p->stall_next ? 1 : 0;
     p->stall_next = false;
     h->edge_capacity = p->edge_cap;
+    h->spill_capacity = 0;
+    h->spill_max = 0;
+    h->pad2 = 0;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;

@@ -21,6 +21,7 @@ constexpr int kRowScanTile = kScanThreads * kRowScanItems;     // copies their r
 constexpr int kWalkThreads = 128;   // collect walk: 4 warps, 32 queries per warp at a time
 constexpr int kFillThreads = 128;   // fill walk: 4 warps (more shared memory per warp)
 constexpr int kMaxDimCells = 32768; // cells along one hashed dimension (float32 key bound)
+constexpr int kSpillSlots = 384;    // neighbour positions kept per long row in the spill area
 
 // Bits of the device status word (1 << frnn_status).
 constexpr unsigned kStNonfinite = 1u << 4;
@@ -46,6 +47,9 @@ struct CallHdr {
     int stall;           // 1: the cell scan's first tile waits for a predecessor that never
                          // publishes, so its bounded waits run out (failure-detection tests)
     long long edge_capacity;
+    long long spill_capacity;  // entries of the neighbour-position spill area (0: none)
+    int spill_max;             // most hits a spilled row may have (0: rows are never spilled)
+    int pad2;
 };
 
 struct EvDesc {
@@ -110,6 +114,14 @@ struct DevState {
     unsigned long long* pool_ctr;  // next free pool slot; zero between builds
     int* edge_off;           // [events_max + 1]
     unsigned* status;
+    // Long rows (more than kFast neighbours) whose neighbours the collect walk
+    // keeps: per chunk that has one, 32 x kSpillSlots positions taken from
+    // spill_ctr; per entry of the emit walk's list, the row's first position
+    // in spill (or -1: walk its candidates again) and its hit count.
+    int* spill;              // [spill_capacity] sorted positions of a long row's neighbours (and itself)
+    unsigned long long* spill_ctr;  // next free spill entry; zero between builds
+    long long* spill_at;     // [n_max]
+    int* spill_n;            // [n_max]
 };
 
 #ifdef __CUDACC__

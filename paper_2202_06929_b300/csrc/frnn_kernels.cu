@@ -823,7 +823,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
     if (MODE == 1) {
         if (threadIdx.x == 0) {
-            *st.pool_ctr = 0ull;                  // the collect walk is done with both
+            *st.pool_ctr = 0ull;                  // the collect walk is done with these
+            if (st.spill_ctr) *st.spill_ctr = 0ull;
             st.counters[kCtrWalkChunks] = 0u;
         }
         // per-event edge offsets, and the capacity check of the emit walk
@@ -1377,8 +1378,9 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int n, i
     __syncwarp();
     for (int k = 2; k <= p2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;  // j is a power of two
             for (int t = lane; t < (p2 >> 1); t += 32) {
-                const int i = 2 * j * (t / j) + (t % j);
+                const int i = ((t >> lj) << (lj + 1)) + (t & (j - 1));
                 const int l = i + j;
                 const unsigned long long x = buf[i], y = buf[l];
                 const bool up = (i & k) == 0;
@@ -1414,7 +1416,7 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 // query-major walk), replaced here by its event-local index before ranking.
 template <bool BY_POS>
 __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long* keys, int raw, bool valid,
-                                          long long q, const LaneEvent& le, int lane)
+                                          long long q, const LaneEvent& le, int lane, long long spill_base = -1)
 {
     const unsigned lt_mask = (1u << lane) - 1u;
     const int K = st.hdr->k;
@@ -1444,7 +1446,23 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
         unsigned lbase = 0;
         if (lane == 0) lbase = atomicAdd(&st.counters[kCtrLongRows], (unsigned)__popc(lm));
         lbase = __shfl_sync(kFull, lbase, 0);
-        if (longrow) st.rank[lbase + __popc(lm & lt_mask)] = (unsigned)q;
+        if (longrow) {
+            const unsigned li = lbase + __popc(lm & lt_mask);
+            st.rank[li] = (unsigned)q;
+            if (st.spill_at) {
+                // a long row whose every hit the walk kept: its first kRowSlots
+                // positions are in the lane's row, the others already in the
+                // spill area behind them
+                long long at = -1;
+                if (spill_base >= 0 && raw > kRowSlots && raw <= st.hdr->spill_max) {
+                    at = spill_base + (long long)lane * kSpillSlots;
+                    const unsigned long long* row = keys + lane * kRowStride;
+                    for (int y = 0; y < kRowSlots; ++y) st.spill[at + y] = (int)(unsigned)row[y];
+                }
+                st.spill_at[li] = at;
+                st.spill_n[li] = raw;
+            }
+        }
     }
     if (BY_POS && my_off >= 0) {
         // sorted position -> event-local index (loads issued four at a time)
@@ -1515,7 +1533,10 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
-    const int kStop = max(st.hdr->k, kRowSlots);  // hits past which a row is long and capped
+    const int spill_max = st.hdr->spill_max;
+    const long long spill_cap = st.hdr->spill_capacity;
+    // hits past which a row is long and capped (no stop when long rows keep every hit)
+    const int kStop = spill_max > 0 ? 0x7fffffff : max(st.hdr->k, kRowSlots);
     const int B = st.hdr->n_events;
     const long long nchunks = (P + 31) >> 5;
     const float4* xs4 = reinterpret_cast<const float4*>(st.xs);
@@ -1547,6 +1568,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
             int nvalid;
             unsigned seg = stage_chunk<DP4>(xs4, q, valid, cs, le.b, sq, lane, &nvalid);
             int deg = 0;
+            long long chunk_spill = -1;  // the chunk's spill area: -1 none yet, -2 none available
             while (seg) {
                 const int a = __ffs(seg) - 1;
                 seg &= seg - 1;
@@ -1569,7 +1591,6 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                         const int cand = candidate_at(rn, base + lane);
                         CandPk<DP4> cp;
                         load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                        const int j = cand >= 0 ? __ldg(st.perm + cand) : 0;
                         const bool cv = cand >= 0;
                         // Every query meets itself exactly once (d2 = 0): it is counted
                         // here and taken out below, which keeps a self test out of this loop.
@@ -1584,8 +1605,27 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                             if (m0 | m1) {
                                 const int s0 = __shfl_sync(kFull, deg, i0) + __popc(m0 & lt_mask);
                                 const int s1 = __shfl_sync(kFull, deg, i1) + __popc(m1 & lt_mask);
-                                if (h0 && s0 < kRowSlots) keys[i0 * kRowStride + s0] = edge_key(d.x, j);
-                                if (h1 && s1 < kRowSlots) keys[i1 * kRowStride + s1] = edge_key(d.y, j);
+                                if (spill_max > 0 && chunk_spill == -1 &&
+                                    __any_sync(kFull, (h0 && s0 >= kRowSlots) || (h1 && s1 >= kRowSlots))) {
+                                    // the chunk's first hit past a row's slots: take its spill area
+                                    long long sb2 = -2;
+                                    if (lane == 0) {
+                                        const unsigned long long got =
+                                            atomicAdd(st.spill_ctr, (unsigned long long)(32 * kSpillSlots));
+                                        if ((long long)got + 32ll * kSpillSlots <= spill_cap) sb2 = (long long)got;
+                                    }
+                                    chunk_spill = __shfl_sync(kFull, sb2, 0);
+                                }
+                                if (h0) {
+                                    if (s0 < kRowSlots) keys[i0 * kRowStride + s0] = edge_key(d.x, cand);
+                                    else if (chunk_spill >= 0 && s0 < spill_max)
+                                        st.spill[chunk_spill + (long long)i0 * kSpillSlots + s0] = cand;
+                                }
+                                if (h1) {
+                                    if (s1 < kRowSlots) keys[i1 * kRowStride + s1] = edge_key(d.y, cand);
+                                    else if (chunk_spill >= 0 && s1 < spill_max)
+                                        st.spill[chunk_spill + (long long)i1 * kSpillSlots + s1] = cand;
+                                }
                                 if (lane == i0) deg += __popc(m0);
                                 if (lane == i1) deg += __popc(m1);
                             }
@@ -1594,7 +1634,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                     }
                 });
             }
-            park_rows<false>(st, keys, deg, valid, q, le, lane);
+            park_rows<true>(st, keys, deg, valid, q, le, lane, chunk_spill);
         }
     }
 }
@@ -1929,8 +1969,156 @@ __device__ __forceinline__ void emit_row_out(const DevState& st, unsigned long l
     __syncwarp();
 }
 
+// Ascending bitonic sort of 32 R keys held in registers: key e sits in lane
+// e % 32, register e / 32.  Partners in other registers of the same lane
+// (distance j >= 32) are swapped in place, with the register pairs fixed at
+// compile time; partners in other lanes are exchanged by shuffles.  Only the
+// loop over registers is unrolled, which keeps the network's code small.
+template <int R>
+__device__ __forceinline__ void reg_bitonic_sort(unsigned long long (&v)[R], int lane)
+{
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int jr = R / 2; jr >= 1; jr >>= 1) {
+            if ((jr << 5) < k) {  // distance 32 jr is one of this k's stages (k/2 down to 32)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if ((r & jr) == 0) {
+                        const int r2 = r | jr;
+                        const bool up = (((r << 5) | lane) & k) == 0;
+                        const unsigned long long a = v[r], b = v[r2];
+                        const bool sw = (a > b) == up;
+                        v[r] = sw ? b : a;
+                        v[r2] = sw ? a : b;
+                    }
+                }
+            }
+        }
+        for (int j = min(k >> 1, 16); j > 0; j >>= 1) {
+            const bool lower = (lane & j) == 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const unsigned long long o = __shfl_xor_sync(kFull, v[r], j);
+                const bool up = (((r << 5) | lane) & k) == 0;
+                v[r] = (lower == up) ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
+            }
+        }
+    }
+}
+
+// The keys of a spilled row, sorted in registers (32 R >= hits), then written
+// out without the query's own key: the smallest cnt of the others.
+template <int DP4, int R>
+__device__ __forceinline__ void emit_spilled_keys(const DevState& st, const ulonglong2 (&qv)[DP4], long long at,
+                                                  int raw, int rs, int cnt, unsigned self_j, int lane)
+{
+    const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
+    unsigned long long v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = (r << 5) | lane;
+        v[r] = ~0ull;
+        if (e < raw) {
+            const int pos = __ldg(st.spill + at + e);
+            ulonglong2 cv[DP4];
+#pragma unroll
+            for (int k = 0; k < DP4; ++k) cv[k] = __ldg(xs2 + (long long)pos * DP4 + k);
+            v[r] = edge_key(dist2_rows<DP4>(qv, cv), __ldg(st.perm + pos));
+        }
+    }
+    reg_bitonic_sort<R>(v, lane);
+    // the query itself (d2 = 0, j = itself) is one of the keys
+    const unsigned long long self_key = (unsigned long long)self_j;
+    int self_idx = raw;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+        const unsigned m = __ballot_sync(kFull, v[r] == self_key);
+        if (m) self_idx = (r << 5) + __ffs(m) - 1;
+    }
+    const int emit = st.hdr->emit_d2;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = (r << 5) | lane;
+        const int o = e - (e > self_idx ? 1 : 0);
+        if (e < raw && e != self_idx && o < cnt) {
+            st.col[rs + o] = (int)(unsigned)v[r];
+            if (emit) st.d2[rs + o] = __uint_as_float((unsigned)(v[r] >> 32));
+        }
+    }
+}
+
+// A long row whose hits the collect walk kept (list entry li, query at
+// sorted position q): each hit's d2 is computed again with the walk's
+// arithmetic, the keys (d2, j) are sorted in registers, and the smallest
+// min(|S_i|, k) other than the query itself are written to the row.
+template <int DP4>
+__device__ void emit_spilled_row(const DevState& st, long long q, int li, unsigned long long* buf, int lane)
+{
+    if constexpr (DP4 <= 4) {
+        const int B = st.hdr->n_events;
+        const int b = event_of_point(st.ev, B, q);
+        const int self_j = __ldg(st.perm + q);
+        const long long p = st.ev[b].pt_off + self_j;
+        const int rs = st.row_ptr[p];
+        const int re = st.row_ptr[p + 1];
+        if ((long long)re > st.hdr->edge_capacity) return;  // over capacity: OVERFLOW already latched
+        const int raw = st.spill_n[li];
+        const long long at = st.spill_at[li];
+        const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
+        ulonglong2 qv[DP4];
+#pragma unroll
+        for (int k = 0; k < DP4; ++k) qv[k] = __ldg(xs2 + q * DP4 + k);
+        const int cnt = re - rs;
+        if (raw <= 64) {
+            emit_spilled_keys<DP4, 2>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
+            return;
+        }
+        if (raw <= 128) {
+            emit_spilled_keys<DP4, 4>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
+            return;
+        }
+        if (raw <= 256) {
+            emit_spilled_keys<DP4, 8>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
+            return;
+        }
+        // more keys than the registers hold: sorted in the warp's buffer
+        // (buf, at least next_pow2(hits) keys)
+        const int emit = st.hdr->emit_d2;
+        __syncwarp();
+        for (int e = lane; e < raw; e += 32) {
+            const int pos = __ldg(st.spill + at + e);
+            ulonglong2 cv[DP4];
+#pragma unroll
+            for (int k = 0; k < DP4; ++k) cv[k] = __ldg(xs2 + (long long)pos * DP4 + k);
+            buf[e] = edge_key(dist2_rows<DP4>(qv, cv), __ldg(st.perm + pos));
+        }
+        __syncwarp();
+        warp_sort_smem(buf, raw, lane);
+        const unsigned long long self_key = (unsigned long long)(unsigned)self_j;
+        int self_idx = raw;
+        for (int e0 = 0; e0 < raw; e0 += 32) {
+            const unsigned m = __ballot_sync(kFull, e0 + lane < raw && buf[e0 + lane] == self_key);
+            if (m) {
+                self_idx = e0 + __ffs(m) - 1;
+                break;
+            }
+        }
+        for (int e = lane; e < raw; e += 32) {
+            if (e == self_idx) continue;
+            const int o = e - (e > self_idx ? 1 : 0);
+            if (o < cnt) {
+                const unsigned long long v = buf[e];
+                st.col[rs + o] = (int)(unsigned)v;
+                if (emit) st.d2[rs + o] = __uint_as_float((unsigned)(v >> 32));
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Stage 7: the long rows (more than kFast neighbours, or no pool space), from
-// the collect walk's list.  A warp takes two consecutive entries; when both
+// the collect walk's list.  Rows whose hits the collect walk kept are sorted
+// from those (emit_spilled_row); the others are walked again.  A warp takes two consecutive entries; when both
 // queries lie in the same cell of the same event (the list follows the cell
 // order, so they usually do) it walks their common candidates once, two
 // queries per packed operation, otherwise one query at a time.  Each row
@@ -1966,8 +2154,23 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
         if (lane == 0) li = (int)atomicAdd(&st.counters[kCtrEmitRows], 2u);
         li = __shfl_sync(kFull, li, 0);
         if (li >= n_long) break;
-        const long long qa = (long long)st.rank[li];
-        const long long qb = li + 1 < n_long ? (long long)st.rank[li + 1] : -1;
+        long long qa = (long long)st.rank[li];
+        long long qb = li + 1 < n_long ? (long long)st.rank[li + 1] : -1;
+        if (st.spill_at) {
+            // rows with their hits kept: from those (one at a time, the warp's
+            // two key buffers as one); the rest by walking again
+            const bool sa = st.spill_at[li] >= 0;
+            const bool sb = qb >= 0 && st.spill_at[li + 1] >= 0;
+            if (sa) emit_spilled_row<DP4>(st, qa, li, keys0, lane);
+            if (sb) emit_spilled_row<DP4>(st, qb, li + 1, keys0, lane);
+            if (sa) {
+                qa = sb ? -1 : qb;
+                qb = -1;
+            } else if (sb) {
+                qb = -1;
+            }
+            if (qa < 0) continue;
+        }
         const int ba = event_of_point(st.ev, B, qa);
         const bool together = qb >= 0 && __ldg(st.cell_s + qa) == __ldg(st.cell_s + qb) &&
                               event_of_point(st.ev, B, qb) == ba;

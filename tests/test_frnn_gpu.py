@@ -161,6 +161,40 @@ def test_single_dense_cell_cap_binds():
     assert_same_as_oracle(x, 0.05, 100)
 
 
+@pytest.mark.parametrize("case", ["dense-k100", "grid-k1024", "dense-nocap", "small-area"])
+def test_long_rows_from_kept_hits(case):
+    """Rows longer than 24 whose every neighbour the walk kept in the plan's
+    spill area (hit_capacity): their k nearest are sorted from those.  With a
+    small area only some chunks get room and the others' rows are walked
+    again; the rows are the oracle's either way."""
+    walk = frnn._native.FRNN_WALK_CANDIDATES
+    if case == "dense-k100":
+        x, r, k, cap = synth.uniform_grid(2500, 3, 9, -6, 6), 0.05, 100, 1 << 22
+    elif case == "grid-k1024":
+        x, r, k, cap = synth.uniform_grid(3000, 2, 17, -40, 40), 0.06, 1024, 1 << 22
+    elif case == "dense-nocap":
+        x, r, k, cap = synth.uniform_grid(4000, 3, 92, -20, 20), 0.05, 0, 1 << 22
+    else:
+        x, r, k, cap = synth.uniform_grid(4000, 3, 93, -12, 12), 0.05, 64, 3 * 32 * 384
+    n, d = x.shape
+    rp, col, d2 = oracle.radius_graph(x, r, k, with_d2=True)
+    assert np.sum(np.diff(rp) > 24) > 100
+    with frnn.Plan(n_max=n, d_max=d, k_max_cap=max(k, 1), emit_d2=True, hit_capacity=cap,
+                   edge_capacity=int(rp[-1]) if k == 0 else 0) as plan:
+        plan.set_tuning(0, 0.0, walk)
+        for rep in range(2):
+            host = plan.build(torch.from_numpy(x).cuda(), r, k).to_host()
+            assert plan.last_status() == 0
+            np.testing.assert_array_equal(host["row_ptr"].astype(np.int64), rp)
+            if k > 0:
+                np.testing.assert_array_equal(host["col"], col)
+                np.testing.assert_array_equal(host["d2"].view(np.uint32), d2.view(np.uint32))
+            else:  # no cap: long rows as sets
+                for i in range(n):
+                    a, b = rp[i], rp[i + 1]
+                    assert sorted(col[a:b].tolist()) == sorted(host["col"][a:b].tolist())
+
+
 def test_points_outside_unit_box_and_large_values():
     rng = np.random.default_rng(4)
     x = (rng.normal(0, 30.0, size=(3000, 4)) + 1000.0).astype(np.float32)

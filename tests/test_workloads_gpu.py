@@ -79,19 +79,25 @@ def _pileup_oracle(name):
 @pytest.mark.parametrize("name", ["c5", "c5b"])
 def test_pileup_scale_event(name):
     """One million points, D=12: a 50,000-query subset equals the oracle, for
-    four and six gridded dims and both walks (c5b: the cap binds for most rows)."""
+    four and six gridded dims and both walks, with long rows walked again or
+    sorted from their kept hits (c5b: the cap binds for most rows)."""
     w = synth.WORKLOADS[name]
     x = synth.make_event(name)
     assert x.shape == (1_000_000, 12)
     q, orp, ocol = _pileup_oracle(name)
     xt = torch.from_numpy(x).cuda()
-    with frnn.Plan(n_max=x.shape[0], d_max=w.d, k_max_cap=w.k, edge_capacity=x.shape[0] * w.k,
-                   cells_per_point=32) as plan:
-        for tuning in [(4, 1.0, WALKS[0]), (4, 1.0, WALKS[1]), (6, 1.0, WALKS[0]), (6, 1.0, WALKS[1])]:
-            plan.set_tuning(*tuning)
-            host = plan.build(xt, w.r, w.k).to_host()
-            assert plan.last_status() == 0
-            _rows_equal(host["row_ptr"].astype(np.int64), host["col"], q, orp, ocol, f"{name} {tuning}")
+    # a plan that keeps the hits of long rows (1.5 GB) and one that walks them again
+    for hits in (0, 32 * 384 * (x.shape[0] // 32 + 1)):
+        with frnn.Plan(n_max=x.shape[0], d_max=w.d, k_max_cap=w.k, edge_capacity=x.shape[0] * w.k,
+                       cells_per_point=32, hit_capacity=hits) as plan:
+            for tuning in [(4, 1.0, WALKS[0]), (4, 1.0, WALKS[1]), (6, 1.0, WALKS[0]), (6, 1.0, WALKS[1])]:
+                if hits and tuning[1:] != (1.0, WALKS[0]):
+                    continue  # only the candidate-major walk keeps hits
+                plan.set_tuning(*tuning)
+                host = plan.build(xt, w.r, w.k).to_host()
+                assert plan.last_status() == 0
+                _rows_equal(host["row_ptr"].astype(np.int64), host["col"], q, orp, ocol,
+                            f"{name} {tuning} hits={hits}")
     capped = np.mean(np.diff(orp) == w.k)
     if name == "c5b":
         assert capped > 0.5, capped     # the cap binds for most rows
