@@ -59,7 +59,7 @@ typedef enum {
 } frnn_status;
 
 /* k_max value that keeps every row whole: the paper's own FRNN list (Sec. 3.4,
- * all points within r, unsorted).  Rows of at most 24 neighbours still come
+ * all points within r, unsorted).  Rows of at most 32 neighbours still come
  * sorted by (d2, j); longer rows are in no particular order.  The edges must
  * fit the plan's edge capacity (FRNN_ERR_OVERFLOW otherwise). */
 #define FRNN_NO_CAP 0

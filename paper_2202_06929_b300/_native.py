@@ -23,7 +23,7 @@ FRNN_ERR_TIMEOUT = 5
 FRNN_ERR_OVERFLOW = 6
 FRNN_ERR_CAPACITY = 7
 
-FRNN_NO_CAP = 0   # k = FRNN_NO_CAP keeps every row whole (rows over 24 neighbours unsorted)
+FRNN_NO_CAP = 0   # k = FRNN_NO_CAP keeps every row whole (rows over 32 neighbours unsorted)
 FRNN_EMIT_D2 = 0x1
 FRNN_USE_GRAPH = 0x2
 FRNN_AUTOTUNE = 0x4

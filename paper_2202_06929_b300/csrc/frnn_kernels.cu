@@ -1042,9 +1042,11 @@ __device__ __forceinline__ void lane_event(const EvDesc* ev, int n_events, long 
 // Per-warp shared-memory state of the walk: the current event's plan (copied
 // when the event changes; indexable without local memory), the cell
 // coordinates of the current segment, and a staging area for run compaction.
-struct WarpWalk {
+struct WalkPlan {
     EvPlan pl;
     int ks[kMaxG];
+};
+struct WarpWalk : WalkPlan {
     int2 stage[32];
 };
 
@@ -1053,7 +1055,7 @@ __device__ __forceinline__ int n_runs(int g)
     return g >= 6 ? 243 : g == 5 ? 81 : g == 4 ? 27 : g == 3 ? 9 : g == 2 ? 3 : 1;
 }
 
-__device__ __forceinline__ void load_plan(WarpWalk& ww, const EvPlan* plan, int b, int lane)
+__device__ __forceinline__ void load_plan(WalkPlan& ww, const EvPlan* plan, int b, int lane)
 {
     __syncwarp();
     if (lane == 0) ww.pl = plan[b];
@@ -1073,7 +1075,7 @@ __device__ __forceinline__ void segment_cell(WarpWalk& ww, const float* qrow, in
 // Run ri of the segment: ri < 3^(g-1) enumerates the offsets {-1,0,1} along
 // the g-1 slower gridded dims; along the fastest dim the cells k-1..k+1 are
 // adjacent in memory, so each combination is one contiguous run of points.
-__device__ __forceinline__ void run_of(const WarpWalk& ww, int ri, const int* cell_start, int& beg, int& len)
+__device__ __forceinline__ void run_of(const WalkPlan& ww, int ri, const int* cell_start, int& beg, int& len)
 {
     const EvPlan& pl = ww.pl;
     const int g = pl.g;
@@ -1414,10 +1416,11 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 // the emit walk, and parks the short rows in the pool sorted and cut at k.
 // BY_POS: the keys' low words hold the candidate's sorted position (the
 // query-major walk), replaced here by its event-local index before ranking.
-template <bool BY_POS>
+template <bool BY_POS, int SLOTS = kRowSlots, int STRIDE = kRowStride>
 __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long* keys, int raw, bool valid,
                                           long long q, const LaneEvent& le, int lane, long long spill_base = -1)
 {
+    constexpr int kFastRow = SLOTS - 1;  // longest row parked from the collected keys
     const unsigned lt_mask = (1u << lane) - 1u;
     const int K = st.hdr->k;
     const int emit = st.hdr->emit_d2;
@@ -1425,7 +1428,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
     // pool space for the chunk's short rows
     const int deg = raw > 0 ? raw - 1 : 0;  // |S_i|
     const int cnt = min(deg, K);
-    const bool fast = valid && deg > 0 && deg <= kFast;
+    const bool fast = valid && deg > 0 && deg <= kFastRow;
     const int need = fast ? cnt : 0;
     const int incl = warp_incl_scan(need, lane);
     const int tot = __shfl_sync(kFull, incl, 31);
@@ -1450,14 +1453,14 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
             const unsigned li = lbase + __popc(lm & lt_mask);
             st.rank[li] = (unsigned)q;
             if (st.spill_at) {
-                // a long row whose every hit the walk kept: its first kRowSlots
+                // a long row whose every hit the walk kept: its first SLOTS
                 // positions are in the lane's row, the others already in the
                 // spill area behind them
                 long long at = -1;
-                if (spill_base >= 0 && raw > kRowSlots && raw <= st.hdr->spill_max) {
+                if (spill_base >= 0 && raw > SLOTS && raw <= st.hdr->spill_max) {
                     at = spill_base + (long long)lane * kSpillSlots;
-                    const unsigned long long* row = keys + lane * kRowStride;
-                    for (int y = 0; y < kRowSlots; ++y) st.spill[at + y] = (int)(unsigned)row[y];
+                    const unsigned long long* row = keys + lane * STRIDE;
+                    for (int y = 0; y < SLOTS; ++y) st.spill[at + y] = (int)(unsigned)row[y];
                 }
                 st.spill_at[li] = at;
                 st.spill_n[li] = raw;
@@ -1466,7 +1469,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
     }
     if (BY_POS && my_off >= 0) {
         // sorted position -> event-local index (loads issued four at a time)
-        unsigned long long* row = keys + lane * kRowStride;
+        unsigned long long* row = keys + lane * STRIDE;
         for (int y = 0; y < raw; y += 4) {
             int jj[4];
 #pragma unroll
@@ -1498,7 +1501,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
             const int cl = __shfl_sync(kFull, cnt, L);
             const unsigned long long self_key = (unsigned long long)(unsigned)__shfl_sync(kFull, self_j, L);
             if (e < tot_in) {
-                const unsigned long long* row = keys + L * kRowStride;
+                const unsigned long long* row = keys + L * STRIDE;
                 const unsigned long long kk = row[e - xin];
                 if (kk != self_key) {
                     int rank = (self_key < kk) ? -1 : 0;
@@ -1656,13 +1659,19 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
 
 constexpr int kRunCap = 256;  // run-list entries per warp
 static_assert(kRunCap >= kMaxRuns, "the runs of any one segment must fit the run list");
+// Rows of this form hold up to 20 neighbours (longer ones go to the emit
+// walk): with 21 slots a warp's shared memory leaves room for 7 blocks of 4
+// warps per SM, as its registers do.  The stride is odd, so the rows of
+// lanes 0..15 start in distinct banks.
+constexpr int kRowSlotsQ = 21;
+constexpr int kRowStrideQ = 21;
 // 8-byte words of shared memory per warp: rows, run list, segment bounds
-constexpr int kQWarpWords = 32 * kRowStride + kRunCap + 32;
+constexpr int kQWarpWords = 32 * kRowStrideQ + kRunCap + 32;
 
 // Appends the non-empty runs of the segment whose cell coordinates are in
 // ww.ks to runs[cnt ..] as (first, end) sorted positions, in run order.
 // Returns false, with cnt unchanged, if they do not all fit the list.
-__device__ __forceinline__ bool append_runs(const WarpWalk& ww, const int2* run_tab, const int* cell_start,
+__device__ __forceinline__ bool append_runs(const WalkPlan& ww, const int2* run_tab, const int* cell_start,
                                             int lane, int2* runs, int& cnt)
 {
     const EvPlan& pl = ww.pl;
@@ -1721,7 +1730,7 @@ __device__ __forceinline__ bool append_runs(const WarpWalk& ww, const int2* run_
 // cs: the lane's cell id.  Returns the bits of the segments listed.
 constexpr int kSegGroup = 8;
 
-__device__ __forceinline__ unsigned list_runs_g4(const WarpWalk& ww, const int2* run_tab, const int* cell_start,
+__device__ __forceinline__ unsigned list_runs_g4(const WalkPlan& ww, const int2* run_tab, const int* cell_start,
                                                  unsigned segs, unsigned cs, int lane, int2* runs, int2* segb,
                                                  int& cnt)
 {
@@ -1807,27 +1816,27 @@ __device__ __forceinline__ void load_row(const ulonglong2* xs2, int pos, ulonglo
 }
 
 template <int DP4>
-__global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
+__global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
 {
     if (timed_out(st)) return;
     extern __shared__ unsigned long long s_qwords[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     unsigned long long* keys = s_qwords + (size_t)wib * kQWarpWords;
-    int2* runs = reinterpret_cast<int2*>(keys + 32 * kRowStride);
+    int2* runs = reinterpret_cast<int2*>(keys + 32 * kRowStrideQ);
     int2* segb = runs + kRunCap;  // per segment (indexed by its first lane): its entries of the run list
-    uint2* my_row2 = reinterpret_cast<uint2*>(keys + lane * kRowStride);  // keys as {low word, high word}
+    uint2* my_row2 = reinterpret_cast<uint2*>(keys + lane * kRowStrideQ);  // keys as {low word, high word}
     const long long P = st.hdr->n_total;
     const float r2 = st.hdr->r2;
-    const int kStop = max(st.hdr->k, kRowSlots);  // hits past which a row is long and capped
+    const int kStop = max(st.hdr->k, kRowSlotsQ);  // hits past which a row is long and capped
     const int B = st.hdr->n_events;
     const long long nchunks = (P + 31) >> 5;
     const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
     LaneEvent le;
     le.lo = 1;
     le.hi = 0;
-    __shared__ WarpWalk s_ww[kWalkThreads / 32];
-    WarpWalk& ww = s_ww[wib];
+    __shared__ WalkPlan s_ww[kWalkThreads / 32];
+    WalkPlan& ww = s_ww[wib];
     int plan_b = -1;
     const long long nwarps = (long long)gridDim.x * (kWalkThreads / 32);
     const unsigned group = nchunks >= 4 * nwarps ? (unsigned)kChunkGroup : 1u;
@@ -1922,9 +1931,9 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
                     const float db = dist2_rows<DP4>(qv, cb);
                     const bool ha = act && da <= r2;
                     const bool hb = act && pb > pos && db <= r2;
-                    if (ha && deg < kRowSlots) my_row2[deg] = make_uint2((unsigned)pos, __float_as_uint(da));
+                    if (ha && deg < kRowSlotsQ) my_row2[deg] = make_uint2((unsigned)pos, __float_as_uint(da));
                     deg += ha;
-                    if (hb && deg < kRowSlots) my_row2[deg] = make_uint2((unsigned)pb, __float_as_uint(db));
+                    if (hb && deg < kRowSlotsQ) my_row2[deg] = make_uint2((unsigned)pb, __float_as_uint(db));
                     deg += hb;
                     pos += 2;
                     const bool adv = pos >= end;
@@ -1941,7 +1950,7 @@ __global__ void __launch_bounds__(kWalkThreads, 6) k_walk_collect_q(DevState st)
                 }
                 __syncwarp();  // the run list is rewritten for the next batch
             }
-            park_rows<true>(st, keys, deg, valid, q, le, lane);
+            park_rows<true, kRowSlotsQ, kRowStrideQ>(st, keys, deg, valid, q, le, lane);
         }
     }
 }
@@ -2216,7 +2225,9 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
             segment_cell(ww, sq, 0, lane);
             const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
             if (K == 0x7fffffff) {
-                // no cap: whole rows, written in candidate order
+                // no cap: whole rows; rows of at most 32 are collected and
+                // sorted, longer ones written in candidate order
+                const bool sm0 = cnt0 <= 32, sm1 = cnt1 <= 32;
                 int nw0 = 0, nw1 = 0;
                 for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
                     for (int base = 0; base < rn.total; base += 32) {
@@ -2232,18 +2243,29 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
                             const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
                             const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
                             if (t0 && s0 < cnt0) {
-                                st.col[rs0 + s0] = j;
-                                if (emit) st.d2[rs0 + s0] = d.x;
+                                if (sm0) {
+                                    keys0[s0] = edge_key(d.x, j);
+                                } else {
+                                    st.col[rs0 + s0] = j;
+                                    if (emit) st.d2[rs0 + s0] = d.x;
+                                }
                             }
                             if (t1 && s1 < cnt1) {
-                                st.col[rs1 + s1] = j;
-                                if (emit) st.d2[rs1 + s1] = d.y;
+                                if (sm1) {
+                                    keys1[s1] = edge_key(d.y, j);
+                                } else {
+                                    st.col[rs1 + s1] = j;
+                                    if (emit) st.d2[rs1 + s1] = d.y;
+                                }
                             }
                             nw0 += __popc(m0);
                             nw1 += __popc(m1);
                         }
                     }
                 });
+                __syncwarp();
+                if (on0 && sm0) emit_row_out(st, keys0, min(nw0, cnt0), rs0, cnt0, emit, lane);
+                if (on1 && sm1) emit_row_out(st, keys1, min(nw1, cnt1), rs1, cnt1, emit, lane);
                 continue;
             }
             unsigned long long thr0 = ~0ull, thr1 = ~0ull;

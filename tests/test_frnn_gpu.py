@@ -419,7 +419,7 @@ def test_plans_with_different_caps_coexist():
 @pytest.mark.parametrize("kind", ["cluster", "dense"])
 def test_no_cap_rows_equal_uncapped_oracle(kind):
     """k = FRNN_NO_CAP: the paper's own FRNN list, every neighbour within r.
-    Rows of at most 24 neighbours are sorted; longer ones are compared as sets."""
+    Rows of at most 32 neighbours are sorted; longer ones are compared as sets."""
     x = (synth.clustered_grid(5000, 8, 91, 300, 0.03, 0.1) if kind == "cluster"
          else synth.uniform_grid(4000, 3, 92, -20, 20))
     r = 0.1 if kind == "cluster" else 0.05
@@ -432,7 +432,7 @@ def test_no_cap_rows_equal_uncapped_oracle(kind):
     long_rows = 0
     for i in range(x.shape[0]):
         a, b = rp[i], rp[i + 1]
-        if b - a <= 24:
+        if b - a <= 32:
             np.testing.assert_array_equal(host["col"][a:b], col[a:b])
             np.testing.assert_array_equal(host["d2"][a:b], d2[a:b])
         else:
