@@ -365,10 +365,9 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     p->stall_next = false;
     h->edge_capacity = p->edge_cap;
     const int cap = next_pow2((k > 32 ? k : 32) + 32);
-    // long rows keep every hit when the plan has room: as many as the emit
-    // walk's two key buffers sort at once (rows of up to 16 floats)
+    // long rows keep every hit when the plan has room (rows of up to 16 floats)
     h->spill_capacity = p->prm.hit_capacity;
-    h->spill_max = (p->prm.hit_capacity > 0 && h->dp / 4 <= 4) ? std::min(kSpillSlots, 2 * cap) : 0;
+    h->spill_max = (p->prm.hit_capacity > 0 && h->dp / 4 <= 4) ? kSpillSlots : 0;
     h->pad2 = 0;
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)

@@ -78,7 +78,8 @@ struct EvPlan {
 
 // Counter slots (all return to zero at the end of every build).
 enum { kCtrPlanned = 0, kCtrScanCellsTile, kCtrScanCellsExit, kCtrScanRowsTile,
-       kCtrScanRowsExit, kCtrLongRows, kCtrWalkChunks, kCtrEmitRows, kCtrLabelCapped, kCtrCount = 16 };
+       kCtrScanRowsExit, kCtrLongRows, kCtrWalkChunks, kCtrEmitRows, kCtrLabelCapped, kCtrKeptRows,
+       kCtrCount = 16 };
 
 // Device pointers owned by the plan.  Fixed for the plan's life, so a
 // captured CUDA graph of the build stays valid for every call: everything
@@ -161,7 +162,7 @@ struct LaunchCfg {
 
 // Host-side launchers (frnn_kernels.cu).  All return a cudaError_t value.
 // stage_events: NULL, or kStages + 1 cudaEvent_t recorded around the stages.
-constexpr int kStages = 7;
+constexpr int kStages = 7;  // the last (emit) stage is two kernels: kept-hit rows, then rows walked again
 // walk: kWalkCandMajor or kWalkQueryMajor (the latter for dp4 <= kMaxDp4QueryMajor only).
 int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, int walk, void* stream, void* stage_events);
 int config_walk(int dp4, int fill_cap, int n_sm, LaunchCfg* cfg);

@@ -1,6 +1,6 @@
 // Kernels of the fixed-radius nearest-neighbour graph build (sm_103a).
 //
-// One build is seven persistent launches on one stream.  Every size is read
+// One build is eight persistent launches on one stream.  Every size is read
 // from the per-call header in device memory, so the launch shapes depend only
 // on the GPU and a captured CUDA graph replays any call within the plan's
 // capacities.  All stages work on a batch of events (a single event is a
@@ -23,8 +23,11 @@
 //                   (d2, j), cut at k and parked in a pool
 //   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr; each parked
 //                   row is copied to its place as soon as its offset is known
-//   7 k_walk_emit   the longer rows, walked again two of a cell per warp,
-//                   keeping the k smallest (d2, j) keys
+//   7 k_emit_kept   the longer rows whose every hit the collect walk kept
+//                   (plans with a hit area): the hits sorted, the k nearest
+//                   written
+//   8 k_walk_emit   the other longer rows, walked again two of a cell per
+//                   warp, keeping the k smallest (d2, j) keys
 //
 // The k-nearest-neighbour build (no radius) reuses stages 1-4 with a
 // density-sized grid, then writes fixed-length row offsets (k_knn_rows) and
@@ -818,6 +821,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevState st)
         if (MODE == 0) {  // the emit walk of the last build is done with both
             st.counters[kCtrLongRows] = 0u;
             st.counters[kCtrEmitRows] = 0u;
+            st.counters[kCtrKeptRows] = 0u;
         }
     }
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) st_relaxed(state + t, 0ull);
@@ -2125,6 +2129,30 @@ __device__ void emit_spilled_row(const DevState& st, long long q, int li, unsign
     }
 }
 
+// Stage 7a: the long rows whose hits the collect walk kept, a warp per row
+// taken from a counter (a kernel of its own: its code stays small).  buf:
+// per warp 2 x kSpillSlots keys of dynamic shared memory for rows with more
+// than 256 hits.
+template <int DP4>
+__global__ void __launch_bounds__(kFillThreads, 8) k_emit_kept(DevState st)
+{
+    if (timed_out(st) || !st.spill_at) return;
+    extern __shared__ unsigned long long s_kept[];
+    const int lane = threadIdx.x & 31;
+    unsigned long long* buf = s_kept + (size_t)(threadIdx.x >> 5) * (2 * kSpillSlots);
+    const int n_long = (int)st.counters[kCtrLongRows];
+    constexpr int kGrab = 16;  // list entries per counter increment (one counter for every warp)
+    for (;;) {
+        int l0 = 0;
+        if (lane == 0) l0 = (int)atomicAdd(&st.counters[kCtrKeptRows], (unsigned)kGrab);
+        l0 = __shfl_sync(kFull, l0, 0);
+        if (l0 >= n_long) break;
+        const int l1 = min(l0 + kGrab, n_long);
+        for (int li = l0; li < l1; ++li)
+            if (st.spill_at[li] >= 0) emit_spilled_row<DP4>(st, (long long)st.rank[li], li, buf, lane);
+    }
+}
+
 // Stage 7: the long rows (more than kFast neighbours, or no pool space), from
 // the collect walk's list.  Rows whose hits the collect walk kept are sorted
 // from those (emit_spilled_row); the others are walked again.  A warp takes two consecutive entries; when both
@@ -2157,156 +2185,159 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
     __shared__ WarpWalk s_ww[kFillThreads / 32];
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
-    // two list entries at a time from a counter (row costs vary widely)
+    // list entries in batches of 8 from a counter (one counter for every
+    // warp), walked two at a time (row costs vary widely, so batches stay small)
+    constexpr int kGrab = 8;
     for (;;) {
-        int li = 0;
-        if (lane == 0) li = (int)atomicAdd(&st.counters[kCtrEmitRows], 2u);
-        li = __shfl_sync(kFull, li, 0);
-        if (li >= n_long) break;
-        long long qa = (long long)st.rank[li];
-        long long qb = li + 1 < n_long ? (long long)st.rank[li + 1] : -1;
-        if (st.spill_at) {
-            // rows with their hits kept: from those (one at a time, the warp's
-            // two key buffers as one); the rest by walking again
-            const bool sa = st.spill_at[li] >= 0;
-            const bool sb = qb >= 0 && st.spill_at[li + 1] >= 0;
-            if (sa) emit_spilled_row<DP4>(st, qa, li, keys0, lane);
-            if (sb) emit_spilled_row<DP4>(st, qb, li + 1, keys0, lane);
-            if (sa) {
-                qa = sb ? -1 : qb;
-                qb = -1;
-            } else if (sb) {
-                qb = -1;
+        int l0 = 0;
+        if (lane == 0) l0 = (int)atomicAdd(&st.counters[kCtrEmitRows], (unsigned)kGrab);
+        l0 = __shfl_sync(kFull, l0, 0);
+        if (l0 >= n_long) break;
+        const int l1 = min(l0 + kGrab, n_long);
+        for (int li = l0; li < l1; li += 2) {
+            long long qa = (long long)st.rank[li];
+            long long qb = li + 1 < l1 ? (long long)st.rank[li + 1] : -1;
+            if (st.spill_at) {
+                // rows with their hits kept were written by k_emit_kept; the
+                // rest are walked again
+                const bool sa = st.spill_at[li] >= 0;
+                const bool sb = qb >= 0 && st.spill_at[li + 1] >= 0;
+                if (sa) {
+                    qa = sb ? -1 : qb;
+                    qb = -1;
+                } else if (sb) {
+                    qb = -1;
+                }
+                if (qa < 0) continue;
             }
-            if (qa < 0) continue;
-        }
-        const int ba = event_of_point(st.ev, B, qa);
-        const bool together = qb >= 0 && __ldg(st.cell_s + qa) == __ldg(st.cell_s + qb) &&
-                              event_of_point(st.ev, B, qb) == ba;
-        // one or two passes: (qa, qb) together, or qa then qb
-        for (int pass = 0; pass < (together || qb < 0 ? 1 : 2); ++pass) {
-            const long long q0 = pass == 0 ? qa : qb;
-            const long long q1 = together ? qb : -1;
-            const int b = pass == 0 ? ba : event_of_point(st.ev, B, q0);
-            const long long pt = st.ev[b].pt_off;
-            int rs0 = 0, cnt0 = 0, rs1 = 0, cnt1 = 0;
-            bool on0, on1 = false;
-            {
-                const long long p = pt + __ldg(st.perm + q0);
-                rs0 = st.row_ptr[p];
-                const int re = st.row_ptr[p + 1];
-                on0 = (long long)re <= ecap;  // over capacity: OVERFLOW already latched
-                cnt0 = re - rs0;
-            }
-            if (q1 >= 0) {
-                const long long p = pt + __ldg(st.perm + q1);
-                rs1 = st.row_ptr[p];
-                const int re = st.row_ptr[p + 1];
-                on1 = (long long)re <= ecap;
-                cnt1 = re - rs1;
-            }
-            if (!on0 && !on1) continue;
-            // the queries' coordinates, interleaved as a pair row (the second
-            // slot repeats the first when the warp walks one query)
-            __syncwarp();
-            if (lane < DP4) {
-                const float4 v = __ldg(xs4 + q0 * DP4 + lane);
-                const float4 u = q1 >= 0 ? __ldg(xs4 + q1 * DP4 + lane) : v;
-                sq[2 * (4 * lane + 0)] = v.x; sq[2 * (4 * lane + 0) + 1] = u.x;
-                sq[2 * (4 * lane + 1)] = v.y; sq[2 * (4 * lane + 1) + 1] = u.y;
-                sq[2 * (4 * lane + 2)] = v.z; sq[2 * (4 * lane + 2) + 1] = u.z;
-                sq[2 * (4 * lane + 3)] = v.w; sq[2 * (4 * lane + 3) + 1] = u.w;
-            }
-            __syncwarp();
-            if (b != plan_b) {
-                load_plan(ww, st.plan, b, lane);
-                plan_b = b;
-            }
-            segment_cell(ww, sq, 0, lane);
-            const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
-            if (K == 0x7fffffff) {
-                // no cap: whole rows; rows of at most 32 are collected and
-                // sorted, longer ones written in candidate order
-                const bool sm0 = cnt0 <= 32, sm1 = cnt1 <= 32;
-                int nw0 = 0, nw1 = 0;
+            const int ba = event_of_point(st.ev, B, qa);
+            const bool together = qb >= 0 && __ldg(st.cell_s + qa) == __ldg(st.cell_s + qb) &&
+                                  event_of_point(st.ev, B, qb) == ba;
+            // one or two passes: (qa, qb) together, or qa then qb
+            for (int pass = 0; pass < (together || qb < 0 ? 1 : 2); ++pass) {
+                const long long q0 = pass == 0 ? qa : qb;
+                const long long q1 = together ? qb : -1;
+                const int b = pass == 0 ? ba : event_of_point(st.ev, B, q0);
+                const long long pt = st.ev[b].pt_off;
+                int rs0 = 0, cnt0 = 0, rs1 = 0, cnt1 = 0;
+                bool on0, on1 = false;
+                {
+                    const long long p = pt + __ldg(st.perm + q0);
+                    rs0 = st.row_ptr[p];
+                    const int re = st.row_ptr[p + 1];
+                    on0 = (long long)re <= ecap;  // over capacity: OVERFLOW already latched
+                    cnt0 = re - rs0;
+                }
+                if (q1 >= 0) {
+                    const long long p = pt + __ldg(st.perm + q1);
+                    rs1 = st.row_ptr[p];
+                    const int re = st.row_ptr[p + 1];
+                    on1 = (long long)re <= ecap;
+                    cnt1 = re - rs1;
+                }
+                if (!on0 && !on1) continue;
+                // the queries' coordinates, interleaved as a pair row (the second
+                // slot repeats the first when the warp walks one query)
+                __syncwarp();
+                if (lane < DP4) {
+                    const float4 v = __ldg(xs4 + q0 * DP4 + lane);
+                    const float4 u = q1 >= 0 ? __ldg(xs4 + q1 * DP4 + lane) : v;
+                    sq[2 * (4 * lane + 0)] = v.x; sq[2 * (4 * lane + 0) + 1] = u.x;
+                    sq[2 * (4 * lane + 1)] = v.y; sq[2 * (4 * lane + 1) + 1] = u.y;
+                    sq[2 * (4 * lane + 2)] = v.z; sq[2 * (4 * lane + 2) + 1] = u.z;
+                    sq[2 * (4 * lane + 3)] = v.w; sq[2 * (4 * lane + 3) + 1] = u.w;
+                }
+                __syncwarp();
+                if (b != plan_b) {
+                    load_plan(ww, st.plan, b, lane);
+                    plan_b = b;
+                }
+                segment_cell(ww, sq, 0, lane);
+                const int2* run_tab = st.run_tab + (size_t)b * kMaxRuns;
+                if (K == 0x7fffffff) {
+                    // no cap: whole rows; rows of at most 32 are collected and
+                    // sorted, longer ones written in candidate order
+                    const bool sm0 = cnt0 <= 32, sm1 = cnt1 <= 32;
+                    int nw0 = 0, nw1 = 0;
+                    for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
+                        for (int base = 0; base < rn.total; base += 32) {
+                            const int cand = candidate_at(rn, base + lane);
+                            CandPk<DP4> cp;
+                            load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
+                            const float2 d = dist2_pair<DP4>(sqp, cp);
+                            const bool t0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                            const bool t1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                            const unsigned m0 = __ballot_sync(kFull, t0);
+                            const unsigned m1 = __ballot_sync(kFull, t1);
+                            if (m0 | m1) {
+                                const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                                const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
+                                if (t0 && s0 < cnt0) {
+                                    if (sm0) {
+                                        keys0[s0] = edge_key(d.x, j);
+                                    } else {
+                                        st.col[rs0 + s0] = j;
+                                        if (emit) st.d2[rs0 + s0] = d.x;
+                                    }
+                                }
+                                if (t1 && s1 < cnt1) {
+                                    if (sm1) {
+                                        keys1[s1] = edge_key(d.y, j);
+                                    } else {
+                                        st.col[rs1 + s1] = j;
+                                        if (emit) st.d2[rs1 + s1] = d.y;
+                                    }
+                                }
+                                nw0 += __popc(m0);
+                                nw1 += __popc(m1);
+                            }
+                        }
+                    });
+                    __syncwarp();
+                    if (on0 && sm0) emit_row_out(st, keys0, min(nw0, cnt0), rs0, cnt0, emit, lane);
+                    if (on1 && sm1) emit_row_out(st, keys1, min(nw1, cnt1), rs1, cnt1, emit, lane);
+                    continue;
+                }
+                unsigned long long thr0 = ~0ull, thr1 = ~0ull;
+                int nk0 = 0, nk1 = 0;
                 for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
                     for (int base = 0; base < rn.total; base += 32) {
                         const int cand = candidate_at(rn, base + lane);
                         CandPk<DP4> cp;
                         load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
                         const float2 d = dist2_pair<DP4>(sqp, cp);
-                        const bool t0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
-                        const bool t1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
-                        const unsigned m0 = __ballot_sync(kFull, t0);
-                        const unsigned m1 = __ballot_sync(kFull, t1);
-                        if (m0 | m1) {
-                            const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
-                            const int s0 = nw0 + __popc(m0 & lt_mask), s1 = nw1 + __popc(m1 & lt_mask);
-                            if (t0 && s0 < cnt0) {
-                                if (sm0) {
-                                    keys0[s0] = edge_key(d.x, j);
-                                } else {
-                                    st.col[rs0 + s0] = j;
-                                    if (emit) st.d2[rs0 + s0] = d.x;
-                                }
-                            }
-                            if (t1 && s1 < cnt1) {
-                                if (sm1) {
-                                    keys1[s1] = edge_key(d.y, j);
-                                } else {
-                                    st.col[rs1 + s1] = j;
-                                    if (emit) st.d2[rs1 + s1] = d.y;
-                                }
-                            }
-                            nw0 += __popc(m0);
-                            nw1 += __popc(m1);
+                        const bool h0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
+                        const bool h1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
+                        if (!__any_sync(kFull, h0 || h1)) continue;
+                        const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
+                        const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
+                        bool t0 = h0 && k0 < thr0, t1 = h1 && k1 < thr1;
+                        unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
+                        if (nk0 + 32 > cap && m0) {
+                            // only reached when |S_i| > k: keep the k smallest so far
+                            warp_sort_smem(keys0, nk0, lane);
+                            nk0 = K;
+                            thr0 = keys0[K - 1];
+                            t0 = t0 && k0 < thr0;
+                            m0 = __ballot_sync(kFull, t0);
                         }
+                        if (nk1 + 32 > cap && m1) {
+                            warp_sort_smem(keys1, nk1, lane);
+                            nk1 = K;
+                            thr1 = keys1[K - 1];
+                            t1 = t1 && k1 < thr1;
+                            m1 = __ballot_sync(kFull, t1);
+                        }
+                        if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
+                        if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
+                        nk0 += __popc(m0);
+                        nk1 += __popc(m1);
+                        __syncwarp();
                     }
                 });
-                __syncwarp();
-                if (on0 && sm0) emit_row_out(st, keys0, min(nw0, cnt0), rs0, cnt0, emit, lane);
-                if (on1 && sm1) emit_row_out(st, keys1, min(nw1, cnt1), rs1, cnt1, emit, lane);
-                continue;
+                if (on0) emit_row_out(st, keys0, nk0, rs0, cnt0, emit, lane);
+                if (on1) emit_row_out(st, keys1, nk1, rs1, cnt1, emit, lane);
             }
-            unsigned long long thr0 = ~0ull, thr1 = ~0ull;
-            int nk0 = 0, nk1 = 0;
-            for_each_run_group(ww, run_tab, st.cell_start, lane, [&](const Runs& rn) {
-                for (int base = 0; base < rn.total; base += 32) {
-                    const int cand = candidate_at(rn, base + lane);
-                    CandPk<DP4> cp;
-                    load_cand<DP4>(xs4 + (long long)(cand < 0 ? 0 : cand) * DP4, cp);
-                    const float2 d = dist2_pair<DP4>(sqp, cp);
-                    const bool h0 = on0 && cand >= 0 && d.x <= r2 && (long long)cand != q0;
-                    const bool h1 = on1 && cand >= 0 && d.y <= r2 && (long long)cand != q1;
-                    if (!__any_sync(kFull, h0 || h1)) continue;
-                    const int j = __ldg(st.perm + (cand < 0 ? 0 : cand));
-                    const unsigned long long k0 = edge_key(d.x, j), k1 = edge_key(d.y, j);
-                    bool t0 = h0 && k0 < thr0, t1 = h1 && k1 < thr1;
-                    unsigned m0 = __ballot_sync(kFull, t0), m1 = __ballot_sync(kFull, t1);
-                    if (nk0 + 32 > cap && m0) {
-                        // only reached when |S_i| > k: keep the k smallest so far
-                        warp_sort_smem(keys0, nk0, lane);
-                        nk0 = K;
-                        thr0 = keys0[K - 1];
-                        t0 = t0 && k0 < thr0;
-                        m0 = __ballot_sync(kFull, t0);
-                    }
-                    if (nk1 + 32 > cap && m1) {
-                        warp_sort_smem(keys1, nk1, lane);
-                        nk1 = K;
-                        thr1 = keys1[K - 1];
-                        t1 = t1 && k1 < thr1;
-                        m1 = __ballot_sync(kFull, t1);
-                    }
-                    if (t0) keys0[nk0 + __popc(m0 & lt_mask)] = k0;
-                    if (t1) keys1[nk1 + __popc(m1 & lt_mask)] = k1;
-                    nk0 += __popc(m0);
-                    nk1 += __popc(m1);
-                    __syncwarp();
-                }
-            });
-            if (on0) emit_row_out(st, keys0, nk0, rs0, cnt0, emit, lane);
-            if (on1) emit_row_out(st, keys1, nk1, rs1, cnt1, emit, lane);
         }
     }
 }
@@ -2649,6 +2680,11 @@ int collect_q_smem()
     return (kWalkThreads / 32) * kQWarpWords * (int)sizeof(unsigned long long);
 }
 
+inline int kept_smem()
+{
+    return (kFillThreads / 32) * 2 * kSpillSlots * (int)sizeof(unsigned long long);
+}
+
 template <int DP4>
 int emit_smem(int cap)
 {
@@ -2670,6 +2706,7 @@ cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, int walk, cud
     mark(ev, 5, s);
     k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 6, s);
+    k_emit_kept<DP4><<<cfg.grid_fill, kFillThreads, kept_smem(), s>>>(st);
     k_walk_emit<DP4><<<cfg.grid_fill, kFillThreads, cfg.fill_smem, s>>>(st, cfg.fill_cap);
     mark(ev, 7, s);
     return cudaGetLastError();
