@@ -1942,7 +1942,8 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                     pos += 2;
                     const bool adv = pos >= end;
                     li += adv;
-                    const int2 rn = runs[min(li, kRunCap - 1)];
+                    int2 rn = make_int2(pos, end);
+                    if (adv && li < hi) rn = runs[li];  // only lanes moving to their next run read it
                     // past kStop hits the row is long (the emit walk takes it) and its count final
                     act = act && li < hi && deg <= kStop;
                     pos = adv ? rn.x : pos;
