@@ -419,6 +419,7 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     unsigned long long b = sizeof(CallHdr) + sizeof(EvDesc) * ev + sizeof(EvPlan) * ev + sizeof(int2) * kMaxRuns * ev;
     b += 2 * sizeof(unsigned) * ev * kMaxDims + 2 * sizeof(unsigned) * ev + sizeof(unsigned) * kCtrCount + 4;
     b += 4 * sizeof(unsigned) * n + sizeof(float) * n * dp + 2 * sizeof(int) * n + sizeof(int) * (n + 1);
+    b += sizeof(unsigned) * (((n + 7) & ~7ull) + 8) + sizeof(FiltPlan) * ev;  // filter keys and plans
     b += sizeof(unsigned) * (unsigned long long)cells_max + sizeof(int) * ((unsigned long long)cells_max + 1);
     b += sizeof(unsigned long long) * (tiles_c + tiles_r);
     b += sizeof(int) * ec * 2 + (d2 ? 2 * sizeof(float) * ec : 0);
@@ -608,6 +609,8 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.perm, n);
     ALLOC(st.cell_s, n);
     ALLOC(st.xs, n * p->dp_max);
+    ALLOC(st.xq, ((n + 7) & ~7LL) + 8);
+    ALLOC(st.fplan, ev);
     ALLOC(st.pool_off, n);
     ALLOC(st.cnt_o, n);
     ALLOC(st.row_ptr, n + 1);

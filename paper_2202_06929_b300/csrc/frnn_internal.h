@@ -76,6 +76,21 @@ struct EvPlan {
     int cell_off;        // first global cell slot of the event
 };
 
+// Written on the device by the planning step (one per event): the
+// candidate filter.  Every point gets a 4-byte key, one byte per filter dim,
+// q_t = floor((x_t - lo_t) * inv_h) with a single step 1 / inv_h for the four
+// dims (the widest dims the grid leaves out first).  For two points within r,
+// sum_t (q_t - q'_t)^2 <= thr, so a candidate whose keys fail that test is
+// skipped without reading its coordinates (the bound is argued in plan_event).
+constexpr int kFiltDims = 4;
+struct FiltPlan {
+    int dim[kFiltDims];  // embedding dim of each key byte, or -1 (byte 0)
+    float lo[kFiltDims];
+    float inv_h;         // 0: every key is 0 (the filter passes everything)
+    int thr;
+    int pad[2];
+};
+
 // Counter slots (all return to zero at the end of every build).
 enum { kCtrPlanned = 0, kCtrScanCellsTile, kCtrScanCellsExit, kCtrScanRowsTile,
        kCtrScanRowsExit, kCtrLongRows, kCtrWalkChunks, kCtrEmitRows, kCtrLabelCapped, kCtrKeptRows,
@@ -101,6 +116,8 @@ struct DevState {
     int* perm;               // [n_max] sorted position -> event-local point index
     unsigned* cell_s;        // [n_max] sorted position -> cell id
     float* xs;               // [n_max * dp_max] points in cell order, rows padded with 0
+    unsigned* xq;            // [roundup(n_max, 8) + 8] filter key of each point, in cell order
+    FiltPlan* fplan;         // [events_max]
     int* pool_off;           // [n_max] point -> first pool slot of its row, or -1
     int* cnt_o;              // [n_max] point -> min(|S_i|, k)
     int* row_ptr;            // [n_max + 1]

@@ -157,6 +157,61 @@ __device__ unsigned block_excl_scan(unsigned v, unsigned* total)
 // --------------------------------------------------------------------------
 // Stage 1: bounding box + per-event plan.
 
+// The candidate filter of an event (FiltPlan).  Key byte t of a point is
+// q_t = floor(a_t), a_t = fl(fl(x_t - lo_t) * inv_h), where lo_t is the event's
+// minimum along the dim and inv_h = fl(254 / w) for the largest extent w of
+// the filter dims, so 0 <= a_t < 255.  The two roundings leave a_t within
+// 255 * 2^-23 < 1e-4 / 2 of the exact (x_t - lo_t) * inv_h, so for two points
+// |q_t - q'_t| < |x_t - x'_t| * inv_h + 1 + 1e-4, and by the triangle
+// inequality over the four dims
+//     sqrt(sum_t (q_t - q'_t)^2) < inv_h * sqrt(D2) + 2 (1 + 1e-4)
+// with D2 the exact squared distance over all dims.  The walks' float32 d2
+// (at most 64 terms, each rounding relative <= 2^-24) is at least
+// D2 (1 - 66 * 2^-24), so a pair with d2 <= r2 has sqrt(D2) <= sqrt(r2) (1 + 2^-17)
+// and its keys satisfy sum_t (q_t - q'_t)^2 <= thr with the margin of
+// thr = floor(((sqrt(r2) inv_h + 2) (1 + 2^-10))^2).  Subnormal ranges
+// (r2 < 2^-100, w < 2^-90), kNN builds and non-finite events get inv_h = 0:
+// every key is 0 and every candidate passes.
+__device__ FiltPlan plan_filter(const EvPlan& pl, const CallHdr& h, const EvDesc& e, const float* w, const float* lo)
+{
+    FiltPlan fp;
+    unsigned long long used = 0ull;  // gridded dims
+    for (int i = 0; i < pl.g; ++i) used |= 1ull << pl.dims[i];
+    // the widest dims the grid leaves out first, then the gridded ones
+    int nf = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (; nf < kFiltDims; ++nf) {
+            int best = -1;
+            float bw = -1.f;
+            for (int t = 0; t < h.d; ++t) {
+                if (((used >> t) & 1ull) != (pass == 1 ? 1ull : 0ull)) continue;
+                bool taken = false;
+                for (int u = 0; u < nf; ++u) taken |= fp.dim[u] == t;
+                if (!taken && w[t] > bw) { bw = w[t]; best = t; }
+            }
+            if (best < 0) break;
+            fp.dim[nf] = best;
+        }
+    }
+    float wmax = 0.f;
+    for (int u = 0; u < kFiltDims; ++u) {
+        if (u >= nf) fp.dim[u] = -1;
+        fp.lo[u] = u < nf ? lo[fp.dim[u]] : 0.f;
+        if (u < nf) wmax = fmaxf(wmax, w[fp.dim[u]]);
+    }
+    fp.inv_h = 0.f;
+    fp.thr = 1 << 30;
+    fp.pad[0] = fp.pad[1] = 0;
+    const bool usable = !pl.skip && !h.knn && e.n > 0 && nf > 0 && wmax >= 0x1p-90f && wmax <= 0x1p100f &&
+                        h.r2 >= 0x1p-100f && h.r2 <= 0x1p100f;
+    if (usable) {
+        fp.inv_h = 254.0f / wmax;
+        const double b = (sqrt((double)h.r2) * (double)fp.inv_h + 2.0) * (1.0 + 0x1p-10);
+        fp.thr = b * b >= (double)(1 << 30) ? (1 << 30) : (int)floor(b * b);
+    }
+    return fp;
+}
+
 // Pick the event's cell grid from its bounding box.  Called by the block that
 // finished the event's last chunk, after a fence.  Correctness never depends
 // on the choice: any grid whose cell edge is at least r (with the margin the
@@ -263,6 +318,7 @@ __device__ void plan_event(const DevState& st, const CallHdr& h, int b, const Ev
             pl.inv_s = 1.0f / s;
         }
         st.plan[b] = pl;
+        st.fplan[b] = plan_filter(pl, h, e, s_w, s_lo);
         s_runs = pl.g;
     }
     __syncthreads();
@@ -884,6 +940,24 @@ __device__ __forceinline__ void copy_row(const float* x, float4* dst, int D, int
     }
 }
 
+// Filter key byte of one coordinate (FiltPlan): floor((x - lo) * inv_h),
+// at most 254 for a finite x of the event (255 for a non-finite one).
+__device__ __forceinline__ unsigned filter_byte(float x, float lo, float inv_h)
+{
+    const float a = __fmul_rn(__fsub_rn(x, lo), inv_h);
+    return a < 255.f ? (unsigned)(int)a : 255u;
+}
+
+// Filter key of a row in global memory.
+__device__ __forceinline__ unsigned filter_key(const FiltPlan& fp, const float* x)
+{
+    unsigned key = 0u;
+#pragma unroll
+    for (int u = 0; u < kFiltDims; ++u)
+        if (fp.dim[u] >= 0) key |= filter_byte(__ldg(x + fp.dim[u]), fp.lo[u], fp.inv_h) << (8 * u);
+    return key;
+}
+
 __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 {
     if (timed_out(st)) return;
@@ -895,6 +969,7 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
         const int cell_off = st.plan[b].cell_off;
+        const FiltPlan fp = st.fplan[b];
         const long long first = (long long)(c - e.chunk_off) * h.chunk;
         const long long rem = (long long)e.n - first;
         const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
@@ -910,13 +985,14 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                     row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
                 }
             }
-            unsigned cid[kPtBatch], rk[kPtBatch];
+            unsigned cid[kPtBatch], rk[kPtBatch], fk[kPtBatch];
 #pragma unroll
             for (int u = 0; u < kPtBatch; ++u) {
                 const int i = i0 + u * kPtThreads;
                 const long long p = e.pt_off + first + (i < np ? i : 0);
                 cid[u] = __ldg(st.key + p);
                 rk[u] = __ldg(st.rank + p);
+                fk[u] = filter_key(fp, h.emb + p * D);
             }
             long long pos[kPtBatch];
 #pragma unroll
@@ -942,6 +1018,7 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                 if (i < np) {
                     st.perm[pos[u]] = (int)(first + i);
                     st.cell_s[pos[u]] = cid[u];
+                    st.xq[pos[u]] = fk[u];
                 }
             }
         }
@@ -1415,14 +1492,16 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 
 // End of a chunk of the collect walk.  Lane i holds query q = q0 + i and
 // raw = its hit count (the query itself included); keys[i * kRowStride ..]
-// holds its first min(raw, kRowSlots) keys in hit order.  Writes every
+// holds its first min(raw, kRowSlots) keys in hit order (complete = false:
+// fewer than that, so the row cannot be parked and goes to the emit walk).  Writes every
 // query's min(|S_i|, k) and pool slot, lists the rows that are not parked for
 // the emit walk, and parks the short rows in the pool sorted and cut at k.
 // BY_POS: the keys' low words hold the candidate's sorted position (the
 // query-major walk), replaced here by its event-local index before ranking.
 template <bool BY_POS, int SLOTS = kRowSlots, int STRIDE = kRowStride>
 __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long* keys, int raw, bool valid,
-                                          long long q, const LaneEvent& le, int lane, long long spill_base = -1)
+                                          long long q, const LaneEvent& le, int lane, long long spill_base = -1,
+                                          bool complete = true)
 {
     constexpr int kFastRow = SLOTS - 1;  // longest row parked from the collected keys
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -1432,7 +1511,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
     // pool space for the chunk's short rows
     const int deg = raw > 0 ? raw - 1 : 0;  // |S_i|
     const int cnt = min(deg, K);
-    const bool fast = valid && deg > 0 && deg <= kFastRow;
+    const bool fast = valid && complete && deg > 0 && deg <= kFastRow;
     const int need = fast ? cnt : 0;
     const int incl = warp_incl_scan(need, lane);
     const int tot = __shfl_sync(kFull, incl, 31);
@@ -1652,14 +1731,14 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
 // A lane per query.  The chunk's segments (queries sharing a cell) first list
 // their non-empty runs of neighbouring cells in shared memory, as many
 // segments at a time as the list holds; then every lane streams its own
-// segment's candidates, two per step, against its query held in registers.
-// Unlike the candidate-major walk there is no vote, shuffle or slot
-// arithmetic per test: a hit is one predicated shared-memory store into the
-// lane's own row.  The price is the spread of candidate counts between the
-// chunk's segments (a lane whose segment has fewer candidates idles at the
-// end).  Rows, the pool and the emit walk's list come out as in the
-// candidate-major walk; keys carry the candidate's sorted position until the
-// row is parked.
+// segment's candidates through the filter (FiltPlan: four one-byte
+// coordinates per point, four candidates per 16-byte load, a few integer
+// operations each), keeping the positions that pass in its row.  Only those
+// (on clustered inputs about as many as the neighbours) are then tested
+// exactly, against the query held in registers.  The price of a lane per
+// query is the spread of candidate counts between the chunk's segments (a
+// lane whose segment has fewer candidates idles at the end).  Rows, the pool
+// and the emit walk's list come out as in the candidate-major walk.
 
 constexpr int kRunCap = 256;  // run-list entries per warp
 static_assert(kRunCap >= kMaxRuns, "the runs of any one segment must fit the run list");
@@ -1731,12 +1810,15 @@ __device__ __forceinline__ bool append_runs(const WalkPlan& ww, const int2* run_
 // are issued before any is used, then the non-empty runs are appended to the
 // run list segment by segment, stopping at the first that does not fit.
 // segs: the segments to list (bits of their first lanes, all of this event);
-// cs: the lane's cell id.  Returns the bits of the segments listed.
+// cs: the lane's cell id; row0, dp: the chunk's first query's sorted row and
+// the row length (a segment's cell coordinates are recomputed from its first
+// query's coordinates with the key kernel's operations).  Returns the bits of
+// the segments listed.
 constexpr int kSegGroup = 8;
 
 __device__ __forceinline__ unsigned list_runs_g4(const WalkPlan& ww, const int2* run_tab, const int* cell_start,
-                                                 unsigned segs, unsigned cs, int lane, int2* runs, int2* segb,
-                                                 int& cnt)
+                                                 unsigned segs, unsigned cs, const float* row0, int dp, int lane,
+                                                 int2* runs, int2* segb, int& cnt)
 {
     const EvPlan& pl = ww.pl;
     const int g = pl.g;
@@ -1756,7 +1838,9 @@ __device__ __forceinline__ unsigned list_runs_g4(const WalkPlan& ww, const int2*
         if (a[u] >= 0) {
             const unsigned c = __shfl_sync(kFull, cs, a[u]);
             // the segment's cell coordinates (lane t: dim t) and the grid faces it lies on
-            const int kt = lane < g ? (int)((c / (unsigned)pl.stride[lane]) % (unsigned)pl.ncell[lane]) : 0;
+            const int kt = lane < g ? cell_coord(__ldg(row0 + a[u] * dp + pl.dims[lane]), pl.lo[lane], pl.inv_s,
+                                                 pl.ncell[lane])
+                                    : 0;
             unsigned face = 0;
             if (lane < g - 1) face = (kt == 0 ? 1u << lane : 0u) | (kt == pl.ncell[lane] - 1 ? 1u << (5 + lane) : 0u);
             const unsigned bad = __reduce_or_sync(kFull, face);
@@ -1781,6 +1865,14 @@ __device__ __forceinline__ unsigned list_runs_g4(const WalkPlan& ww, const int2*
         listed |= 1u << a[u];
     }
     return listed;
+}
+
+// The filter test of a candidate key c against a query key qk (FiltPlan):
+// sum_t (qk_t - c_t)^2 <= thr, written as sum c_t^2 - 2 sum qk_t c_t <= thr_a
+// with thr_a = thr - sum qk_t^2 (byte dot products, exact in 32 bits).
+__device__ __forceinline__ bool filter_pass(unsigned c, unsigned qk, int thr_a)
+{
+    return (int)__dp4a(c, c, 0u) - 2 * (int)__dp4a(qk, c, 0u) <= thr_a;
 }
 
 // d2 of a query against a candidate row, both as pairs of dims (a float4 is
@@ -1864,7 +1956,11 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
             const bool start = valid && (lane == 0 || cs != up_cs || le.b != up_b);
             const unsigned segm = __ballot_sync(kFull, start);
             const int my_a = 31 - __clz(segm & (kFull >> (31 - lane)));  // first lane of this lane's segment
-            int deg = 0;
+            // the query's filter key and its share of the event's threshold
+            const unsigned qk = __ldg(st.xq + (valid ? q : 0));
+            const int thr_a = __ldg(&st.fplan[le.b].thr) - (int)__dp4a(qk, qk, 0u);
+            int np = 0;     // candidates that passed the filter
+            int extra = 0;  // hits among those past the row's slots
             unsigned todo = segm;
             while (todo) {
                 // list the runs of as many segments as fit (the first always does)
@@ -1890,7 +1986,8 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                         unsigned grp = same;
                         for (int u = kSegGroup; u > 0 && grp; --u) grp &= grp - 1;
                         grp = same & ~grp;  // its first kSegGroup segments
-                        listed = list_runs_g4(ww, run_tab, st.cell_start, grp, cs, lane, runs, segb, cnt);
+                        listed = list_runs_g4(ww, run_tab, st.cell_start, grp, cs, st.xs + (ch << 5) * (4 * DP4),
+                                              4 * DP4, lane, runs, segb, cnt);
                         if (listed != grp) {  // the list is full
                             batch |= listed;
                             todo &= ~listed;
@@ -1911,12 +2008,14 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                     todo &= ~listed;
                 }
                 __syncwarp();
-                // every lane of the batch streams its segment's candidates, two
-                // per step.  The step is branch-free: a lane with no work left
-                // (or none in this batch) runs it on a valid row with its hits
-                // masked, and a lane at the end of a run takes the next one by
-                // selection.  A key is stored as the pair {position, d2 bits},
-                // i.e. the 64-bit value (d2 bits << 32) | position.
+                // Every lane of the batch streams its segment's candidates
+                // through the filter, eight keys (one 32-byte load) per step:
+                // a key that passes puts the candidate's position in the
+                // lane's row (past the row's slots the candidate is tested at
+                // once).  The step is branch-free apart from storing the
+                // passes: a lane with no work left (or none in this batch)
+                // loads a valid sector with its slots masked, and a lane at
+                // the end of a run takes the next one by selection.
                 int li = 0, hi = 0;
                 if (valid && ((batch >> my_a) & 1u)) {
                     const int2 sbd = segb[my_a];
@@ -1927,25 +2026,41 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                 const int2 r0 = runs[act ? li : 0];
                 int pos = act ? r0.x : 0, end = act ? r0.y : 1;
                 while (__any_sync(kFull, act)) {
-                    const int pb = min(pos + 1, end - 1);  // the run's last point twice when it is odd
-                    ulonglong2 ca[DP4], cb[DP4];
-                    load_row<DP4>(xs2, pos, ca);
-                    load_row<DP4>(xs2, pb, cb);
-                    const float da = dist2_rows<DP4>(qv, ca);
-                    const float db = dist2_rows<DP4>(qv, cb);
-                    const bool ha = act && da <= r2;
-                    const bool hb = act && pb > pos && db <= r2;
-                    if (ha && deg < kRowSlotsQ) my_row2[deg] = make_uint2((unsigned)pos, __float_as_uint(da));
-                    deg += ha;
-                    if (hb && deg < kRowSlotsQ) my_row2[deg] = make_uint2((unsigned)pb, __float_as_uint(db));
-                    deg += hb;
-                    pos += 2;
+                    const int sb = pos & ~7;
+                    unsigned long long k01, k23, k45, k67;
+                    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+                        : "=l"(k01), "=l"(k23), "=l"(k45), "=l"(k67)
+                        : "l"(st.xq + sb));
+                    const int nhi = end - sb;  // slots [pos - sb, min(nhi, 8)) are the run's
+                    unsigned pm = (filter_pass((unsigned)k01, qk, thr_a) ? 1u : 0u) |
+                                  (filter_pass((unsigned)(k01 >> 32), qk, thr_a) ? 2u : 0u) |
+                                  (filter_pass((unsigned)k23, qk, thr_a) ? 4u : 0u) |
+                                  (filter_pass((unsigned)(k23 >> 32), qk, thr_a) ? 8u : 0u) |
+                                  (filter_pass((unsigned)k45, qk, thr_a) ? 16u : 0u) |
+                                  (filter_pass((unsigned)(k45 >> 32), qk, thr_a) ? 32u : 0u) |
+                                  (filter_pass((unsigned)k67, qk, thr_a) ? 64u : 0u) |
+                                  (filter_pass((unsigned)(k67 >> 32), qk, thr_a) ? 128u : 0u);
+                    pm &= (0xffu << (pos - sb)) & (nhi >= 8 ? 0xffu : (1u << nhi) - 1u);
+                    pm = act ? pm : 0u;
+                    while (pm) {
+                        const int p = sb + __ffs(pm) - 1;
+                        pm &= pm - 1;
+                        if (np < kRowSlotsQ) {
+                            my_row2[np].x = (unsigned)p;
+                        } else {
+                            ulonglong2 cv[DP4];
+                            load_row<DP4>(xs2, p, cv);
+                            extra += dist2_rows<DP4>(qv, cv) <= r2;
+                        }
+                        ++np;
+                    }
+                    pos = sb + 8;
                     const bool adv = pos >= end;
                     li += adv;
                     int2 rn = make_int2(pos, end);
                     if (adv && li < hi) rn = runs[li];  // only lanes moving to their next run read it
                     // past kStop hits the row is long (the emit walk takes it) and its count final
-                    act = act && li < hi && deg <= kStop;
+                    act = act && li < hi && extra <= kStop;
                     pos = adv ? rn.x : pos;
                     end = adv ? rn.y : end;
                     if (!act) {
@@ -1955,7 +2070,26 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                 }
                 __syncwarp();  // the run list is rewritten for the next batch
             }
-            park_rows<true, kRowSlotsQ, kRowStrideQ>(st, keys, deg, valid, q, le, lane);
+            // The candidates kept in the row, tested exactly (two at a time,
+            // loads first); a hit is rewritten in place as its key
+            // {event-local index, d2 bits}.
+            int nh = 0;
+            const int nkeep = min(np, kRowSlotsQ);
+            for (int y = 0; y < nkeep; y += 2) {
+                const int pa = (int)my_row2[y].x;
+                const int pb = (y + 1 < nkeep) ? (int)my_row2[y + 1].x : pa;
+                ulonglong2 ca[DP4], cb[DP4];
+                load_row<DP4>(xs2, pa, ca);
+                load_row<DP4>(xs2, pb, cb);
+                const int ja = __ldg(st.perm + pa), jb = __ldg(st.perm + pb);
+                const float da = dist2_rows<DP4>(qv, ca);
+                const float db = dist2_rows<DP4>(qv, cb);
+                if (da <= r2) my_row2[nh++] = make_uint2((unsigned)ja, __float_as_uint(da));
+                if (y + 1 < nkeep && db <= r2) my_row2[nh++] = make_uint2((unsigned)jb, __float_as_uint(db));
+            }
+            // a row with more passes than slots is not complete in shared memory
+            park_rows<false, kRowSlotsQ, kRowStrideQ>(st, keys, nh + extra, valid, q, le, lane, -1,
+                                                      np <= kRowSlotsQ);
         }
     }
 }

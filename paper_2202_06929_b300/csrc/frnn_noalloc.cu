@@ -60,7 +60,9 @@ constexpr size_t kOffCellS = align256(kOffPerm + sizeof(int) * kNoallocMaxPoints
 constexpr size_t kOffPoolOff = align256(kOffCellS + sizeof(unsigned) * kNoallocMaxPoints);
 constexpr size_t kOffCntO = align256(kOffPoolOff + sizeof(int) * kNoallocMaxPoints);
 constexpr size_t kOffXs = align256(kOffCntO + sizeof(int) * kNoallocMaxPoints);
-constexpr size_t kOffCellCount = align256(kOffXs + sizeof(float) * kNoallocMaxPoints * kNoallocMaxDims);
+constexpr size_t kOffXq = align256(kOffXs + sizeof(float) * kNoallocMaxPoints * kNoallocMaxDims);
+constexpr size_t kOffFplan = align256(kOffXq + sizeof(unsigned) * (kNoallocMaxPoints + 8));
+constexpr size_t kOffCellCount = align256(kOffFplan + sizeof(FiltPlan));
 constexpr size_t kOffCellStart = align256(kOffCellCount + sizeof(unsigned) * kNoallocCells);
 constexpr long long kTilesCells = kNoallocCells / kScanTile + 1;
 constexpr long long kTilesRows = kNoallocMaxPoints / kRowScanTile + 1;
@@ -186,6 +188,8 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     st.perm = reinterpret_cast<int*>(b + kOffPerm);
     st.cell_s = reinterpret_cast<unsigned*>(b + kOffCellS);
     st.xs = reinterpret_cast<float*>(b + kOffXs);
+    st.xq = reinterpret_cast<unsigned*>(b + kOffXq);
+    st.fplan = reinterpret_cast<FiltPlan*>(b + kOffFplan);
     st.pool_off = reinterpret_cast<int*>(b + kOffPoolOff);
     st.cnt_o = reinterpret_cast<int*>(b + kOffCntO);
     st.row_ptr = row_ptr;

@@ -213,6 +213,35 @@ def test_extreme_caps(k):
     assert_same_as_oracle(x, 0.06, k)
 
 
+@pytest.mark.parametrize("outlier", [False, True])
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
+def test_pairs_at_the_radius_along_filter_dims(outlier, walk):
+    """Partners placed at distances within a few ulps of r, displaced only
+    along the dims the grid leaves out (those the one-byte key filter reads),
+    off the 1/256 grid.  With outliers (five points at 100 along dims 0-4)
+    only one dim is gridded and the filter's key step is about 4 r, so most
+    candidates pass the filter and rows overflow their slots (the candidates
+    past them are tested at once).  The key filter may only skip pairs
+    farther than r, so every row still equals the oracle's."""
+    rng = np.random.default_rng(2202)
+    n0, d, r = 1200, 8, 0.1
+    base = rng.uniform(-1, 1, size=(n0, d)).astype(np.float32)
+    parts = [base]
+    for scale in (1 - 2**-22, 1.0, 1 + 2**-22, 1 - 2**-12, 1 + 2**-12):
+        u = rng.normal(size=(n0, d))
+        u[:, :4] = 0.0  # the four widest dims are gridded; move along the others
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        parts.append((base + (r * scale) * u).astype(np.float32))
+    x = np.concatenate(parts)
+    x[:, :4] *= np.float32(1.5)  # keep dims 0-3 the widest
+    if outlier:
+        for t in range(5):
+            x[t, t] = np.float32(100.0)
+    x = x[rng.permutation(x.shape[0])]
+    host = assert_same_as_oracle(x, r, 16, tuning=(4, 1.0, walk))
+    assert host["row_ptr"][-1] > 0
+
+
 def test_radius_boundary_inclusive():
     x = np.array([[0.0, 0.0], [0.125, 0.0], [0.0, 0.12890625]], dtype=np.float32)
     host = assert_same_as_oracle(x, 0.125, 4)
