@@ -80,8 +80,8 @@ struct EvPlan {
 // candidate filter.  Every point gets a 4-byte key, one byte per filter dim,
 // q_t = floor((x_t - lo_t) * inv_h) with a single step 1 / inv_h for the four
 // dims (the widest dims the grid leaves out first).  For two points within r,
-// sum_t (q_t - q'_t)^2 <= thr, so a candidate whose keys fail that test is
-// skipped without reading its coordinates (the bound is argued in plan_event).
+// sum_t |q_t - q'_t| <= thr, so a candidate whose keys fail that test is
+// skipped without reading its coordinates (the bound is argued in plan_filter).
 constexpr int kFiltDims = 4;
 struct FiltPlan {
     int dim[kFiltDims];  // embedding dim of each key byte, or -1 (byte 0)

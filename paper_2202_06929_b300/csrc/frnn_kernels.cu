@@ -162,14 +162,14 @@ __device__ unsigned block_excl_scan(unsigned v, unsigned* total)
 // minimum along the dim and inv_h = fl(254 / w) for the largest extent w of
 // the filter dims, so 0 <= a_t < 255.  The two roundings leave a_t within
 // 255 * 2^-23 < 1e-4 / 2 of the exact (x_t - lo_t) * inv_h, so for two points
-// |q_t - q'_t| < |x_t - x'_t| * inv_h + 1 + 1e-4, and by the triangle
-// inequality over the four dims
-//     sqrt(sum_t (q_t - q'_t)^2) < inv_h * sqrt(D2) + 2 (1 + 1e-4)
+// |q_t - q'_t| < |x_t - x'_t| * inv_h + 1 + 1e-4, and summed over the four
+// dims, with sum_t |a_t| <= 2 sqrt(sum_t a_t^2) (Cauchy-Schwarz),
+//     sum_t |q_t - q'_t| < 2 inv_h * sqrt(D2) + 4 (1 + 1e-4)
 // with D2 the exact squared distance over all dims.  The walks' float32 d2
 // (at most 64 terms, each rounding relative <= 2^-24) is at least
 // D2 (1 - 66 * 2^-24), so a pair with d2 <= r2 has sqrt(D2) <= sqrt(r2) (1 + 2^-17)
-// and its keys satisfy sum_t (q_t - q'_t)^2 <= thr with the margin of
-// thr = floor(((sqrt(r2) inv_h + 2) (1 + 2^-10))^2).  Subnormal ranges
+// and its keys satisfy sum_t |q_t - q'_t| <= thr with the margin of
+// thr = floor((2 sqrt(r2) inv_h + 4) (1 + 2^-10)).  Subnormal ranges
 // (r2 < 2^-100, w < 2^-90), kNN builds and non-finite events get inv_h = 0:
 // every key is 0 and every candidate passes.
 __device__ FiltPlan plan_filter(const EvPlan& pl, const CallHdr& h, const EvDesc& e, const float* w, const float* lo)
@@ -206,8 +206,8 @@ __device__ FiltPlan plan_filter(const EvPlan& pl, const CallHdr& h, const EvDesc
                         h.r2 >= 0x1p-100f && h.r2 <= 0x1p100f;
     if (usable) {
         fp.inv_h = 254.0f / wmax;
-        const double b = (sqrt((double)h.r2) * (double)fp.inv_h + 2.0) * (1.0 + 0x1p-10);
-        fp.thr = b * b >= (double)(1 << 30) ? (1 << 30) : (int)floor(b * b);
+        const double b = (2.0 * sqrt((double)h.r2) * (double)fp.inv_h + 4.0) * (1.0 + 0x1p-10);
+        fp.thr = b >= (double)(1 << 30) ? (1 << 30) : (int)floor(b);
     }
     return fp;
 }
@@ -1492,8 +1492,7 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 
 // End of a chunk of the collect walk.  Lane i holds query q = q0 + i and
 // raw = its hit count (the query itself included); keys[i * kRowStride ..]
-// holds its first min(raw, kRowSlots) keys in hit order (complete = false:
-// fewer than that, so the row cannot be parked and goes to the emit walk).  Writes every
+// holds its first min(raw, kRowSlots) keys in hit order.  Writes every
 // query's min(|S_i|, k) and pool slot, lists the rows that are not parked for
 // the emit walk, and parks the short rows in the pool sorted and cut at k.
 // BY_POS: the keys' low words hold the candidate's sorted position (the
@@ -1868,11 +1867,10 @@ __device__ __forceinline__ unsigned list_runs_g4(const WalkPlan& ww, const int2*
 }
 
 // The filter test of a candidate key c against a query key qk (FiltPlan):
-// sum_t (qk_t - c_t)^2 <= thr, written as sum c_t^2 - 2 sum qk_t c_t <= thr_a
-// with thr_a = thr - sum qk_t^2 (byte dot products, exact in 32 bits).
-__device__ __forceinline__ bool filter_pass(unsigned c, unsigned qk, int thr_a)
+// sum_t |qk_t - c_t| <= thr, one byte-wise sum of absolute differences.
+__device__ __forceinline__ bool filter_pass(unsigned c, unsigned qk, int thr)
 {
-    return (int)__dp4a(c, c, 0u) - 2 * (int)__dp4a(qk, c, 0u) <= thr_a;
+    return (int)__vsadu4(qk, c) <= thr;
 }
 
 // d2 of a query against a candidate row, both as pairs of dims (a float4 is
@@ -1947,18 +1945,15 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
             const bool valid = q < P;
             lane_event(st.ev, B, valid ? q : P - 1, le);
             const unsigned cs = valid ? __ldg(st.cell_s + q) : 0xffffffffu;
-            ulonglong2 qv[DP4];
-#pragma unroll
-            for (int k = 0; k < DP4; ++k) qv[k] = __ldg(xs2 + (valid ? q : 0) * DP4 + k);
             // segments: runs of lanes with the same cell and event
             const unsigned up_cs = __shfl_up_sync(kFull, cs, 1);
             const int up_b = __shfl_up_sync(kFull, le.b, 1);
             const bool start = valid && (lane == 0 || cs != up_cs || le.b != up_b);
             const unsigned segm = __ballot_sync(kFull, start);
             const int my_a = 31 - __clz(segm & (kFull >> (31 - lane)));  // first lane of this lane's segment
-            // the query's filter key and its share of the event's threshold
+            // the query's filter key and the event's threshold
             const unsigned qk = __ldg(st.xq + (valid ? q : 0));
-            const int thr_a = __ldg(&st.fplan[le.b].thr) - (int)__dp4a(qk, qk, 0u);
+            const int thr = __ldg(&st.fplan[le.b].thr);
             int np = 0;     // candidates that passed the filter
             int extra = 0;  // hits among those past the row's slots
             unsigned todo = segm;
@@ -2032,14 +2027,14 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                         : "=l"(k01), "=l"(k23), "=l"(k45), "=l"(k67)
                         : "l"(st.xq + sb));
                     const int nhi = end - sb;  // slots [pos - sb, min(nhi, 8)) are the run's
-                    unsigned pm = (filter_pass((unsigned)k01, qk, thr_a) ? 1u : 0u) |
-                                  (filter_pass((unsigned)(k01 >> 32), qk, thr_a) ? 2u : 0u) |
-                                  (filter_pass((unsigned)k23, qk, thr_a) ? 4u : 0u) |
-                                  (filter_pass((unsigned)(k23 >> 32), qk, thr_a) ? 8u : 0u) |
-                                  (filter_pass((unsigned)k45, qk, thr_a) ? 16u : 0u) |
-                                  (filter_pass((unsigned)(k45 >> 32), qk, thr_a) ? 32u : 0u) |
-                                  (filter_pass((unsigned)k67, qk, thr_a) ? 64u : 0u) |
-                                  (filter_pass((unsigned)(k67 >> 32), qk, thr_a) ? 128u : 0u);
+                    unsigned pm = (filter_pass((unsigned)k01, qk, thr) ? 1u : 0u) |
+                                  (filter_pass((unsigned)(k01 >> 32), qk, thr) ? 2u : 0u) |
+                                  (filter_pass((unsigned)k23, qk, thr) ? 4u : 0u) |
+                                  (filter_pass((unsigned)(k23 >> 32), qk, thr) ? 8u : 0u) |
+                                  (filter_pass((unsigned)k45, qk, thr) ? 16u : 0u) |
+                                  (filter_pass((unsigned)(k45 >> 32), qk, thr) ? 32u : 0u) |
+                                  (filter_pass((unsigned)k67, qk, thr) ? 64u : 0u) |
+                                  (filter_pass((unsigned)(k67 >> 32), qk, thr) ? 128u : 0u);
                     pm &= (0xffu << (pos - sb)) & (nhi >= 8 ? 0xffu : (1u << nhi) - 1u);
                     pm = act ? pm : 0u;
                     while (pm) {
@@ -2048,9 +2043,10 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                         if (np < kRowSlotsQ) {
                             my_row2[np].x = (unsigned)p;
                         } else {
-                            ulonglong2 cv[DP4];
+                            ulonglong2 qw[DP4], cv[DP4];
+                            load_row<DP4>(xs2, (int)q, qw);
                             load_row<DP4>(xs2, p, cv);
-                            extra += dist2_rows<DP4>(qv, cv) <= r2;
+                            extra += dist2_rows<DP4>(qw, cv) <= r2;
                         }
                         ++np;
                     }
@@ -2075,6 +2071,8 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
             // {event-local index, d2 bits}.
             int nh = 0;
             const int nkeep = min(np, kRowSlotsQ);
+            ulonglong2 qv[DP4];
+            load_row<DP4>(xs2, valid ? (int)q : 0, qv);
             for (int y = 0; y < nkeep; y += 2) {
                 const int pa = (int)my_row2[y].x;
                 const int pb = (y + 1 < nkeep) ? (int)my_row2[y + 1].x : pa;
