@@ -2319,8 +2319,11 @@ __global__ void __launch_bounds__(kFillThreads, DP4 <= 4 ? 7 : 2) k_walk_emit(De
     WarpWalk& ww = s_ww[wib];
     int plan_b = -1;
     // list entries in batches of 8 from a counter (one counter for every
-    // warp), walked two at a time (row costs vary widely, so batches stay small)
-    constexpr int kGrab = 8;
+    // warp), walked two at a time (row costs vary widely, so batches stay
+    // small); two at a time when the list is short, so that it still spreads
+    // over every warp
+    const int nwarps = (int)(gridDim.x * (kFillThreads / 32));
+    const int kGrab = n_long >= 8 * nwarps ? 8 : 2;
     for (;;) {
         int l0 = 0;
         if (lane == 0) l0 = (int)atomicAdd(&st.counters[kCtrEmitRows], (unsigned)kGrab);
