@@ -270,6 +270,16 @@ int chunk_points(const frnn_plan* p, long long n_total)
     return c;
 }
 
+// Chunks the bounding-box kernel takes at a time: its per-chunk reduction,
+// barriers and atomics cost about as much as reading a chunk, so a batch much
+// larger than the grid is read a few chunks (of one event) per step.
+int bbox_group(const frnn_plan* p, int chunks)
+{
+    int g = 1;
+    while (g < 8 && chunks > 2ll * g * p->base_cfg.grid_pt) g *= 2;
+    return g;
+}
+
 int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
                      int d, float r, int k, frnn_csr* out, long long* n_total)
 {
@@ -368,7 +378,7 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     // long rows keep every hit when the plan has room (rows of up to 16 floats)
     h->spill_capacity = p->prm.hit_capacity;
     h->spill_max = (p->prm.hit_capacity > 0 && h->dp / 4 <= 4) ? kSpillSlots : 0;
-    h->pad2 = 0;
+    h->bbox_group = bbox_group(p, chunks);
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;
@@ -788,7 +798,7 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     h->edge_capacity = p->edge_cap;
     h->spill_capacity = 0;
     h->spill_max = 0;
-    h->pad2 = 0;
+    h->bbox_group = bbox_group(p, chunks);
     const size_t bytes = sizeof(CallHdr) + sizeof(EvDesc) * (size_t)n_events;
     if (cudaMemcpyAsync(p->d_call, p->h_call[slot], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FRNN_ERR_CUDA;

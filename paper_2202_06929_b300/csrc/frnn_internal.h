@@ -49,7 +49,7 @@ struct CallHdr {
     long long edge_capacity;
     long long spill_capacity;  // entries of the neighbour-position spill area (0: none)
     int spill_max;             // most hits a spilled row may have (0: rows are never spilled)
-    int pad2;
+    int bbox_group;            // consecutive chunks the bounding-box kernel takes at a time (0: 1)
 };
 
 struct EvDesc {

@@ -1,6 +1,6 @@
 // Kernels of the fixed-radius nearest-neighbour graph build (sm_103a).
 //
-// One build is eight persistent launches on one stream.  Every size is read
+// One build is nine persistent launches on one stream.  Every size is read
 // from the per-call header in device memory, so the launch shapes depend only
 // on the GPU and a captured CUDA graph replays any call within the plan's
 // capacities.  All stages work on a batch of events (a single event is a
@@ -15,7 +15,8 @@
 //   3 k_scan<0>     exclusive scan of the cell histogram (decoupled look-back
 //                   per block tile), which also clears the histogram
 //   4 k_scatter     points copied into cell order, rows padded to a multiple
-//                   of four floats for 16-byte loads
+//                   of four floats for 16-byte loads; k_filter_keys then
+//                   writes each point's one-byte-per-dim filter key
 //   5 k_walk_collect  warps take chunks of 32 queries in cell order from a
 //                   counter; per cell they walk the 3^(g-1) runs of
 //                   neighbouring cells and count the points within r
@@ -375,105 +376,114 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
     __shared__ int s_nf, s_last, s_last_planner;
     const CallHdr h = *st.hdr;
     const int D = h.d;
-    for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
-        const int b = event_of_chunk(st.ev, h.n_events, c);
-        const EvDesc e = st.ev[b];
-        for (int t = threadIdx.x; t < D; t += blockDim.x) {
-            s_min[t] = 0xffffffffu;
-            s_max[t] = 0u;
-        }
-        if (threadIdx.x == 0) s_nf = 0;
-        __syncthreads();
-        const long long first = (long long)(c - e.chunk_off) * h.chunk;
-        const long long rem = (long long)e.n - first;
-        const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
-        const float* base = h.emb + (e.pt_off + first) * D;
-        const int nel = np * D;
-        bool nf = false;
-        const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
-        if (vec) {
-            // float4 loads; with S a multiple of D / 4, every float4 this
-            // thread reads holds dims 4 (threadIdx.x % (D / 4)) .. + 3
-            const int q4 = D >> 2;
-            const int S = (kPtThreads / q4) * q4;
-            const float4* b4 = reinterpret_cast<const float4*>(base);
-            const int n4 = np * q4;
-            unsigned mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mn3 = 0xffffffffu;
-            unsigned mx0 = 0u, mx1 = 0u, mx2 = 0u, mx3 = 0u;
-            if ((int)threadIdx.x < S) {
-#pragma unroll 8
-                for (int i = threadIdx.x; i < n4; i += S) {
-                    const float4 v = __ldg(b4 + i);
-                    nf |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
-                    const unsigned u0 = f2ord(v.x), u1 = f2ord(v.y), u2 = f2ord(v.z), u3 = f2ord(v.w);
-                    mn0 = min(mn0, u0); mx0 = max(mx0, u0);
-                    mn1 = min(mn1, u1); mx1 = max(mx1, u1);
-                    mn2 = min(mn2, u2); mx2 = max(mx2, u2);
-                    mn3 = min(mn3, u3); mx3 = max(mx3, u3);
-                }
-                if ((int)threadIdx.x < n4) {
-                    const int d0 = 4 * ((int)threadIdx.x % q4);
-                    atomicMin(&s_min[d0 + 0], mn0); atomicMax(&s_max[d0 + 0], mx0);
-                    atomicMin(&s_min[d0 + 1], mn1); atomicMax(&s_max[d0 + 1], mx1);
-                    atomicMin(&s_min[d0 + 2], mn2); atomicMax(&s_max[d0 + 2], mx2);
-                    atomicMin(&s_min[d0 + 3], mn3); atomicMax(&s_max[d0 + 3], mx3);
-                }
-            }
-        } else {
-            // with S a multiple of D, every element this thread reads belongs
-            // to dim threadIdx.x % D
-            const int S = (kPtThreads / D) * D;
-            unsigned lmin = 0xffffffffu, lmax = 0u;
-            if ((int)threadIdx.x < S) {
-#pragma unroll 4
-                for (int i = threadIdx.x; i < nel; i += S) {
-                    const float v = __ldg(base + i);
-                    nf |= !isfinite(v);
-                    const unsigned u = f2ord(v);
-                    lmin = min(lmin, u);
-                    lmax = max(lmax, u);
-                }
-                if ((int)threadIdx.x < nel) {
-                    atomicMin(&s_min[threadIdx.x % D], lmin);
-                    atomicMax(&s_max[threadIdx.x % D], lmax);
-                }
-            }
-        }
-        if (nf) s_nf = 1;
-        __syncthreads();
-        if (np > 0) {
+    // a block takes G consecutive chunks at a time and reduces the ones of
+    // each event among them together
+    const int G = h.bbox_group > 1 ? h.bbox_group : 1;
+    for (int c0 = blockIdx.x * G; c0 < h.total_chunks; c0 += gridDim.x * G) {
+        const int c_end = min(c0 + G, h.total_chunks);
+        for (int c = c0; c < c_end;) {
+            const int b = event_of_chunk(st.ev, h.n_events, c);
+            const EvDesc e = st.ev[b];
+            const int c1 = min(c_end, e.chunk_off + e.nchunk);  // this event's chunks of the group: [c, c1)
             for (int t = threadIdx.x; t < D; t += blockDim.x) {
-                atomicMin(&st.bb_min[b * kMaxDims + t], s_min[t]);
-                atomicMax(&st.bb_max[b * kMaxDims + t], s_max[t]);
+                s_min[t] = 0xffffffffu;
+                s_max[t] = 0u;
             }
-        }
-        if (threadIdx.x == 0 && s_nf) atomicOr(&st.nonfinite[b], 1u);
-        // the barrier orders every thread's atomics before thread 0's fence,
-        // which publishes them before the chunk is counted
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned done = atomicAdd(&st.chunk_done[b], 1u);
-            s_last = (done == (unsigned)e.nchunk - 1u);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            plan_event(st, h, b, e);
+            if (threadIdx.x == 0) s_nf = 0;
+            __syncthreads();
+            const long long first = (long long)(c - e.chunk_off) * h.chunk;
+            const long long rem = (long long)e.n - first;
+            const long long span = (long long)(c1 - c) * h.chunk;
+            const int np = (int)(rem < 0 ? 0 : (rem > span ? span : rem));
+            const float* base = h.emb + (e.pt_off + first) * D;
+            const int nel = np * D;
+            bool nf = false;
+            const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
+            if (vec) {
+                // float4 loads; with S a multiple of D / 4, every float4 this
+                // thread reads holds dims 4 (threadIdx.x % (D / 4)) .. + 3
+                const int q4 = D >> 2;
+                const int S = (kPtThreads / q4) * q4;
+                const float4* b4 = reinterpret_cast<const float4*>(base);
+                const int n4 = np * q4;
+                unsigned mn0 = 0xffffffffu, mn1 = 0xffffffffu, mn2 = 0xffffffffu, mn3 = 0xffffffffu;
+                unsigned mx0 = 0u, mx1 = 0u, mx2 = 0u, mx3 = 0u;
+                if ((int)threadIdx.x < S) {
+    #pragma unroll 8
+                    for (int i = threadIdx.x; i < n4; i += S) {
+                        const float4 v = __ldg(b4 + i);
+                        nf |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+                        const unsigned u0 = f2ord(v.x), u1 = f2ord(v.y), u2 = f2ord(v.z), u3 = f2ord(v.w);
+                        mn0 = min(mn0, u0); mx0 = max(mx0, u0);
+                        mn1 = min(mn1, u1); mx1 = max(mx1, u1);
+                        mn2 = min(mn2, u2); mx2 = max(mx2, u2);
+                        mn3 = min(mn3, u3); mx3 = max(mx3, u3);
+                    }
+                    if ((int)threadIdx.x < n4) {
+                        const int d0 = 4 * ((int)threadIdx.x % q4);
+                        atomicMin(&s_min[d0 + 0], mn0); atomicMax(&s_max[d0 + 0], mx0);
+                        atomicMin(&s_min[d0 + 1], mn1); atomicMax(&s_max[d0 + 1], mx1);
+                        atomicMin(&s_min[d0 + 2], mn2); atomicMax(&s_max[d0 + 2], mx2);
+                        atomicMin(&s_min[d0 + 3], mn3); atomicMax(&s_max[d0 + 3], mx3);
+                    }
+                }
+            } else {
+                // with S a multiple of D, every element this thread reads belongs
+                // to dim threadIdx.x % D
+                const int S = (kPtThreads / D) * D;
+                unsigned lmin = 0xffffffffu, lmax = 0u;
+                if ((int)threadIdx.x < S) {
+    #pragma unroll 4
+                    for (int i = threadIdx.x; i < nel; i += S) {
+                        const float v = __ldg(base + i);
+                        nf |= !isfinite(v);
+                        const unsigned u = f2ord(v);
+                        lmin = min(lmin, u);
+                        lmax = max(lmax, u);
+                    }
+                    if ((int)threadIdx.x < nel) {
+                        atomicMin(&s_min[threadIdx.x % D], lmin);
+                        atomicMax(&s_max[threadIdx.x % D], lmax);
+                    }
+                }
+            }
+            if (nf) s_nf = 1;
+            __syncthreads();
+            if (np > 0) {
+                for (int t = threadIdx.x; t < D; t += blockDim.x) {
+                    atomicMin(&st.bb_min[b * kMaxDims + t], s_min[t]);
+                    atomicMax(&st.bb_max[b * kMaxDims + t], s_max[t]);
+                }
+            }
+            if (threadIdx.x == 0 && s_nf) atomicOr(&st.nonfinite[b], 1u);
+            // the barrier orders every thread's atomics before thread 0's fence,
+            // which publishes them before the chunk is counted
             __syncthreads();
             if (threadIdx.x == 0) {
-                if (st.plan[b].skip) atomicOr(st.status, kStNonfinite);
                 __threadfence();
-                const unsigned pl = atomicAdd(&st.counters[kCtrPlanned], 1u);
-                s_last_planner = (pl == (unsigned)h.n_events - 1u);
+                const unsigned done = atomicAdd(&st.chunk_done[b], (unsigned)(c1 - c));
+                s_last = (done + (unsigned)(c1 - c) == (unsigned)e.nchunk);
             }
             __syncthreads();
-            if (s_last_planner) {
+            if (s_last) {
                 __threadfence();
-                place_cell_tables(st, h.n_events);
+                plan_event(st, h, b, e);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    if (st.plan[b].skip) atomicOr(st.status, kStNonfinite);
+                    __threadfence();
+                    const unsigned pl = atomicAdd(&st.counters[kCtrPlanned], 1u);
+                    s_last_planner = (pl == (unsigned)h.n_events - 1u);
+                }
+                __syncthreads();
+                if (s_last_planner) {
+                    __threadfence();
+                    place_cell_tables(st, h.n_events);
+                }
             }
+            __syncthreads();
+            c = c1;
         }
-        __syncthreads();
     }
 }
 
@@ -969,7 +979,6 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
         const int cell_off = st.plan[b].cell_off;
-        const FiltPlan fp = st.fplan[b];
         const long long first = (long long)(c - e.chunk_off) * h.chunk;
         const long long rem = (long long)e.n - first;
         const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
@@ -985,14 +994,13 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                     row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
                 }
             }
-            unsigned cid[kPtBatch], rk[kPtBatch], fk[kPtBatch];
+            unsigned cid[kPtBatch], rk[kPtBatch];
 #pragma unroll
             for (int u = 0; u < kPtBatch; ++u) {
                 const int i = i0 + u * kPtThreads;
                 const long long p = e.pt_off + first + (i < np ? i : 0);
                 cid[u] = __ldg(st.key + p);
                 rk[u] = __ldg(st.rank + p);
-                fk[u] = filter_key(fp, h.emb + p * D);
             }
             long long pos[kPtBatch];
 #pragma unroll
@@ -1018,9 +1026,29 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                 if (i < np) {
                     st.perm[pos[u]] = (int)(first + i);
                     st.cell_s[pos[u]] = cid[u];
-                    st.xq[pos[u]] = fk[u];
                 }
             }
+        }
+    }
+}
+
+// Stage 4b: the filter key of every point, in cell order (FiltPlan), from
+// its sorted row (a warp reads 32 consecutive rows).
+__global__ void __launch_bounds__(kPtThreads) k_filter_keys(DevState st)
+{
+    if (timed_out(st)) return;
+    const CallHdr h = *st.hdr;
+    const int dp = h.dp;
+    for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
+        const int b = event_of_chunk(st.ev, h.n_events, c);
+        const EvDesc e = st.ev[b];
+        const FiltPlan fp = st.fplan[b];
+        const long long first = (long long)(c - e.chunk_off) * h.chunk;
+        const long long rem = (long long)e.n - first;
+        const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
+        for (int i = threadIdx.x; i < np; i += kPtThreads) {
+            const long long p = e.pt_off + first + i;
+            st.xq[p] = filter_key(fp, st.xs + p * dp);
         }
     }
 }
@@ -2906,6 +2934,7 @@ int launch_build(const DevState& st, int dp4, const LaunchCfg& cfg, int walk, vo
     k_scan<0><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
     mark(ev, 3, s);
     k_scatter<<<cfg.grid_scatter, kPtThreads, 0, s>>>(st);
+    k_filter_keys<<<cfg.grid_pt, kPtThreads, 0, s>>>(st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     switch (dp4) {
