@@ -1520,12 +1520,15 @@ __device__ __forceinline__ unsigned long long edge_key(float d2, int j)
 
 // End of a chunk of the collect walk.  Lane i holds query q = q0 + i and
 // raw = its hit count (the query itself included); keys[i * kRowStride ..]
-// holds its first min(raw, kRowSlots) keys in hit order.  Writes every
+// holds its first min(raw, kRowSlots) keys in hit order (SELF_IN_ROW =
+// false: the keys of the other hits only, raw - 1 of them).  Writes every
 // query's min(|S_i|, k) and pool slot, lists the rows that are not parked for
 // the emit walk, and parks the short rows in the pool sorted and cut at k.
 // BY_POS: the keys' low words hold the candidate's sorted position (the
-// query-major walk), replaced here by its event-local index before ranking.
-template <bool BY_POS, int SLOTS = kRowSlots, int STRIDE = kRowStride>
+// candidate-major walk), replaced here by its event-local index before
+// ranking.  complete = false: the row holds fewer keys than that, so it is
+// not parked and goes to the emit walk.
+template <bool BY_POS, int SLOTS = kRowSlots, int STRIDE = kRowStride, bool SELF_IN_ROW = true>
 __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long* keys, int raw, bool valid,
                                           long long q, const LaneEvent& le, int lane, long long spill_base = -1,
                                           bool complete = true)
@@ -1597,7 +1600,7 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
     // row is the number of the row's keys below it, less one if the query's
     // own key (d2 = 0, j = itself) is among them.
     if (fits) {
-        const int nin = my_off >= 0 ? raw : 0;
+        const int nin = my_off >= 0 ? (SELF_IN_ROW ? raw : raw - 1) : 0;
         const int incl_in = warp_incl_scan(nin, lane);
         const int tot_in = __shfl_sync(kFull, incl_in, 31);
         const int excl_in = incl_in - nin;
@@ -1613,8 +1616,8 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
             if (e < tot_in) {
                 const unsigned long long* row = keys + L * STRIDE;
                 const unsigned long long kk = row[e - xin];
-                if (kk != self_key) {
-                    int rank = (self_key < kk) ? -1 : 0;
+                if (!SELF_IN_ROW || kk != self_key) {
+                    int rank = (SELF_IN_ROW && self_key < kk) ? -1 : 0;
 #pragma unroll 4
                     for (int y = 0; y < nl; ++y) rank += row[y] < kk;
                     if (rank < cl) {
@@ -2097,7 +2100,7 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
             // The candidates kept in the row, tested exactly (two at a time,
             // loads first); a hit is rewritten in place as its key
             // {event-local index, d2 bits}.
-            int nh = 0;
+            int nh = 0, self = 0;
             const int nkeep = min(np, kRowSlotsQ);
             ulonglong2 qv[DP4];
             load_row<DP4>(xs2, valid ? (int)q : 0, qv);
@@ -2110,12 +2113,21 @@ __global__ void __launch_bounds__(kWalkThreads, 7) k_walk_collect_q(DevState st)
                 const int ja = __ldg(st.perm + pa), jb = __ldg(st.perm + pb);
                 const float da = dist2_rows<DP4>(qv, ca);
                 const float db = dist2_rows<DP4>(qv, cb);
-                if (da <= r2) my_row2[nh++] = make_uint2((unsigned)ja, __float_as_uint(da));
-                if (y + 1 < nkeep && db <= r2) my_row2[nh++] = make_uint2((unsigned)jb, __float_as_uint(db));
+                // the query itself (always a hit) is counted but not kept
+                if (da <= r2) {
+                    if (pa != (int)q) my_row2[nh] = make_uint2((unsigned)ja, __float_as_uint(da));
+                    nh += pa != (int)q;
+                    self += pa == (int)q;
+                }
+                if (y + 1 < nkeep && db <= r2) {
+                    if (pb != (int)q) my_row2[nh] = make_uint2((unsigned)jb, __float_as_uint(db));
+                    nh += pb != (int)q;
+                    self += pb == (int)q;
+                }
             }
             // a row with more passes than slots is not complete in shared memory
-            park_rows<false, kRowSlotsQ, kRowStrideQ>(st, keys, nh + extra, valid, q, le, lane, -1,
-                                                      np <= kRowSlotsQ);
+            park_rows<false, kRowSlotsQ, kRowStrideQ, false>(st, keys, nh + self + extra, valid, q, le, lane, -1,
+                                                             np <= kRowSlotsQ && self == 1);
         }
     }
 }
