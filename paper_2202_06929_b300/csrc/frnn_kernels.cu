@@ -975,6 +975,7 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
     const int D = h.d, dp = h.dp;
     const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
     const bool vec8 = D == 8 && ((reinterpret_cast<uintptr_t>(h.emb) & 31) == 0);  // xs rows are 32-byte aligned
+    const bool vec12 = D == 12 && vec;  // rows of three float4s (xs rows 48 bytes, 16-byte aligned)
     for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
@@ -984,14 +985,25 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
         const int np = (int)(rem < 0 ? 0 : (rem > h.chunk ? h.chunk : rem));
         for (int i0 = threadIdx.x; i0 < np; i0 += kPtThreads * kPtBatch) {
             // D = 8 (rows of 32 bytes, the input 32-byte aligned): one 32-byte
-            // load per row, issued with the key and rank loads, before the
-            // cell-table loads that depend on them
+            // load per row; D = 12: three 16-byte loads.  Issued with the key
+            // and rank loads, before the cell-table loads that depend on them
             F8 row[kPtBatch];
+            float4 tail[kPtBatch];
             if (vec8) {
 #pragma unroll
                 for (int u = 0; u < kPtBatch; ++u) {
                     const int i = i0 + u * kPtThreads;
                     row[u] = ld_nc_f8(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 8);
+                }
+            } else if (vec12) {
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    const float4* x4 = reinterpret_cast<const float4*>(h.emb + (e.pt_off + first + (i < np ? i : 0)) * 12);
+                    const float4 a = __ldg(x4), b4 = __ldg(x4 + 1);
+                    tail[u] = __ldg(x4 + 2);
+                    row[u].v[0] = a.x; row[u].v[1] = a.y; row[u].v[2] = a.z; row[u].v[3] = a.w;
+                    row[u].v[4] = b4.x; row[u].v[5] = b4.y; row[u].v[6] = b4.z; row[u].v[7] = b4.w;
                 }
             }
             unsigned cid[kPtBatch], rk[kPtBatch];
@@ -1010,6 +1022,17 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                 for (int u = 0; u < kPtBatch; ++u) {
                     const int i = i0 + u * kPtThreads;
                     if (i < np) st_f8(st.xs + pos[u] * 8, row[u]);
+                }
+            } else if (vec12) {
+#pragma unroll
+                for (int u = 0; u < kPtBatch; ++u) {
+                    const int i = i0 + u * kPtThreads;
+                    if (i < np) {
+                        float4* d4 = reinterpret_cast<float4*>(st.xs + pos[u] * 12);
+                        d4[0] = make_float4(row[u].v[0], row[u].v[1], row[u].v[2], row[u].v[3]);
+                        d4[1] = make_float4(row[u].v[4], row[u].v[5], row[u].v[6], row[u].v[7]);
+                        d4[2] = tail[u];
+                    }
                 }
             } else {
 #pragma unroll
