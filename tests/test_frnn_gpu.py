@@ -242,6 +242,35 @@ def test_pairs_at_the_radius_along_filter_dims(outlier, walk):
     assert host["row_ptr"][-1] > 0
 
 
+@pytest.mark.parametrize("case", ["flat-filter-dims", "tiny-radius", "huge-extent", "three-dims"])
+@pytest.mark.parametrize("walk", WALKS, ids=WALK_IDS)
+def test_key_filter_degenerate_events(case, walk):
+    """Events where the key filter has nothing to go on, or is switched off:
+    the dims it reads are constant (every key equal), the radius is so small
+    that r^2 is below 2^-100, the extent is beyond 2^100, or every dim is
+    gridded (the filter then reads gridded dims).  The rows still equal the
+    oracle's."""
+    rng = np.random.default_rng(77)
+    if case == "flat-filter-dims":
+        x = rng.uniform(-1, 1, size=(3000, 8)).astype(np.float32)
+        x[:, 4:] = np.float32(0.25)
+        x[:, :4] *= np.float32(0.3)
+        r, k = 0.1, 32
+    elif case == "tiny-radius":
+        base = rng.uniform(-1, 1, size=(1500, 8)).astype(np.float32)
+        x = np.concatenate([base, base[:700]])  # exact duplicates: d2 = 0 <= r2
+        r, k = 1e-16, 8
+    elif case == "huge-extent":
+        base = (rng.normal(0, 1, size=(2000, 8)) * 1e30).astype(np.float32)
+        x = np.concatenate([base, base[:600]])  # at this scale only duplicates are within r
+        r, k = 1e18, 16
+    else:
+        x = synth.uniform_grid(4000, 3, 12, -40, 40)
+        r, k = 0.05, 24
+    x = x[rng.permutation(x.shape[0])]
+    assert_same_as_oracle(x, r, k, tuning=(0, 0.0, walk))
+
+
 def test_radius_boundary_inclusive():
     x = np.array([[0.0, 0.0], [0.125, 0.0], [0.0, 0.12890625]], dtype=np.float32)
     host = assert_same_as_oracle(x, 0.125, 4)
