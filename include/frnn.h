@@ -329,7 +329,7 @@ FRNN_API int frnn_plan_test_stall_next_build(frnn_plan* plan);
  * (code running inside a framework that owns all device memory and forbids
  * allocation after start-up, or whose device memory is fixed at
  * initialisation).  The caller passes the points and the outputs; every other
- * buffer lives in one array of about 11.5 MB in device memory that each
+ * buffer lives in one array of about 12.5 MB in device memory that each
  * device loading the library holds until the process exits.
  *   emb          device float32 [n][d], row-major, caller-owned.
  *   n <= 32768, d <= 16, k_max <= 64; larger sizes return FRNN_ERR_CAPACITY

@@ -69,7 +69,7 @@ constexpr long long kTilesRows = kNoallocMaxPoints / kRowScanTile + 1;
 constexpr size_t kOffScanCells = align256(kOffCellStart + sizeof(int) * (kNoallocCells + 1));
 constexpr size_t kOffScanRows = align256(kOffScanCells + sizeof(unsigned long long) * kTilesCells);
 constexpr size_t kOffPool = align256(kOffScanRows + sizeof(unsigned long long) * kTilesRows);
-constexpr size_t kArenaBytes = align256(kOffPool + sizeof(int) * kNoallocPool);  // about 11.5 MB
+constexpr size_t kArenaBytes = align256(kOffPool + sizeof(int) * kNoallocPool);  // about 12.5 MB
 
 // The scratch of every call on this device (see the file comment).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kArenaBytes];
