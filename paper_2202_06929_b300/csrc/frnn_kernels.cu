@@ -17,11 +17,15 @@
 //   4 k_scatter     points copied into cell order, rows padded to a multiple
 //                   of four floats for 16-byte loads; k_filter_keys then
 //                   writes each point's one-byte-per-dim filter key
-//   5 k_walk_collect  warps take chunks of 32 queries in cell order from a
-//                   counter; per cell they walk the 3^(g-1) runs of
-//                   neighbouring cells and count the points within r
-//                   (|S_i|); rows of at most kFast neighbours are sorted by
-//                   (d2, j), cut at k and parked in a pool
+//   5 k_walk_collect_q / k_walk_collect  warps take chunks of 32 queries
+//                   in cell order from a counter; per cell they walk the
+//                   3^(g-1) runs of neighbouring cells and count the points
+//                   within r (|S_i|); short rows are sorted by (d2, j), cut
+//                   at k and parked in a pool.  The query-major form (a lane
+//                   per query) tests each candidate's filter key first and
+//                   the float32 distance only where the key passes; the
+//                   candidate-major form (candidates across the lanes) can
+//                   keep every hit of a long row for stage 7
 //   6 k_scan<1>     exclusive scan of min(|S_i|, k) into row_ptr; each parked
 //                   row is copied to its place as soon as its offset is known
 //   7 k_emit_kept   the longer rows whose every hit the collect walk kept
