@@ -119,8 +119,10 @@ typedef struct {
  *                            neighbourhood at a time, tested against the
  *                            cell's queries two per packed operation;
  *   FRNN_WALK_QUERIES (2)    a lane per query, each streaming the candidates
- *                            of its own cell's neighbourhood (d <= 12; larger
- *                            d falls back to FRNN_WALK_CANDIDATES).
+ *                            of its own cell's neighbourhood through a
+ *                            one-byte-per-dim key filter and testing only the
+ *                            ones that pass exactly (d <= 12; larger d falls
+ *                            back to FRNN_WALK_CANDIDATES).
  */
 #define FRNN_WALK_AUTO 0
 #define FRNN_WALK_CANDIDATES 1
@@ -235,7 +237,8 @@ FRNN_API int frnn_build_graph_host(frnn_plan* plan, const float* h_emb, const in
  * for profiling.  Never replays a CUDA graph.  Synchronous: waits for the
  * build, then writes the device time of each stage in milliseconds to
  * stage_ms[0..6]: bounding box and cell grid, cell ids and histogram, cell
- * scan, scatter into cell order, collect walk, row scan, emit walk.
+ * scan, scatter into cell order (with the filter keys), collect walk, row
+ * scan, emit walk.
  * n_stages must be >= 7.  Errors: as frnn_build_graph_batched.
  */
 FRNN_API int frnn_build_graph_profiled(frnn_plan* plan, const float* emb, const int64_t* ev_off,
