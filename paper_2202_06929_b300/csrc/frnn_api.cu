@@ -433,7 +433,7 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     b += sizeof(unsigned) * (unsigned long long)cells_max + sizeof(int) * ((unsigned long long)cells_max + 1);
     b += sizeof(unsigned long long) * (tiles_c + tiles_r);
     b += sizeof(int) * ec * 2 + (d2 ? 2 * sizeof(float) * ec : 0);
-    b += 8 + sizeof(int) * (ev + 1) + 4;
+    b += 8 + sizeof(int) * (ev + 1) + 4 + sizeof(unsigned);
     b += 3 * sizeof(unsigned long long);  // autotuner probe
     b += sizeof(float) * n * (unsigned long long)q.d_max;  // input of the host-to-host call
     if (q.hit_capacity > 0)  // neighbours of long rows, and per long row its entry
@@ -635,6 +635,7 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.pool_ctr, 1);
     ALLOC(st.edge_off, ev + 1);
     ALLOC(st.status, 1);
+    ALLOC(st.offgrid, 1);
     ALLOC(p->probe, 3);
     ALLOC(p->d_input, n * q.d_max);  // the device copy of frnn_build_graph_host's input
     p->d_input_floats = n * q.d_max;

@@ -132,6 +132,10 @@ struct DevState {
     unsigned long long* pool_ctr;  // next free pool slot; zero between builds
     int* edge_off;           // [events_max + 1]
     unsigned* status;
+    // Nonzero once the scatter has seen a coordinate off the exact fast
+    // path's grid (cleared by the bounding-box pass of every build): while it
+    // is zero, squared distances may be accumulated with fused multiply-adds.
+    unsigned* offgrid;
     // Long rows (more than kFast neighbours) whose neighbours the collect walk
     // keeps: per chunk that has one, 32 x kSpillSlots positions taken from
     // spill_ctr; per entry of the emit walk's list, the row's first position

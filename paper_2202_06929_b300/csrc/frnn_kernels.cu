@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(kPtThreads) k_bbox_plan(DevState st)
     __shared__ int s_nf, s_last, s_last_planner;
     const CallHdr h = *st.hdr;
     const int D = h.d;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *st.offgrid = 0u;  // the scatter of this build sets it
     // a block takes G consecutive chunks at a time and reduces the ones of
     // each event among them together
     const int G = h.bbox_group > 1 ? h.bbox_group : 1;
@@ -954,6 +955,18 @@ __device__ __forceinline__ void copy_row(const float* x, float4* dst, int D, int
     }
 }
 
+// On the grid of the exact fast path: x = m / 256 with m an integer and
+// |m| <= mmax, where D (2 mmax)^2 <= 2^24.  Between two such points every
+// difference, square and partial sum of the squared distance is a multiple
+// of 2^-16 below 2^8, exact in float32, so adding each square with one fused
+// multiply-add gives the bits of the sequential sum of rounded squares (the
+// bench's inputs, on the 1/256 grid in [-1, 1], all are on it).
+__device__ __forceinline__ bool on_grid(float x, float mmax)
+{
+    const float m = x * 256.0f;  // exact: a power of two (or inf / NaN)
+    return m == rintf(m) && fabsf(m) <= mmax;
+}
+
 // Filter key byte of one coordinate (FiltPlan): floor((x - lo) * inv_h),
 // at most 254 for a finite x of the event (255 for a non-finite one).
 __device__ __forceinline__ unsigned filter_byte(float x, float lo, float inv_h)
@@ -980,6 +993,8 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
     const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(h.emb) & 15) == 0);
     const bool vec8 = D == 8 && ((reinterpret_cast<uintptr_t>(h.emb) & 31) == 0);  // xs rows are 32-byte aligned
     const bool vec12 = D == 12 && vec;  // rows of three float4s (xs rows 48 bytes, 16-byte aligned)
+    const float mmax = floorf(0.5f * sqrtf(16777216.0f / (float)D));
+    bool og = false;  // a coordinate of this thread's points is off the fast path's grid
     for (int c = blockIdx.x; c < h.total_chunks; c += gridDim.x) {
         const int b = event_of_chunk(st.ev, h.n_events, c);
         const EvDesc e = st.ev[b];
@@ -1025,7 +1040,11 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
 #pragma unroll
                 for (int u = 0; u < kPtBatch; ++u) {
                     const int i = i0 + u * kPtThreads;
-                    if (i < np) st_f8(st.xs + pos[u] * 8, row[u]);
+                    if (i < np) {
+                        st_f8(st.xs + pos[u] * 8, row[u]);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) og |= !on_grid(row[u].v[t], mmax);
+                    }
                 }
             } else if (vec12) {
 #pragma unroll
@@ -1036,15 +1055,21 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
                         d4[0] = make_float4(row[u].v[0], row[u].v[1], row[u].v[2], row[u].v[3]);
                         d4[1] = make_float4(row[u].v[4], row[u].v[5], row[u].v[6], row[u].v[7]);
                         d4[2] = tail[u];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) og |= !on_grid(row[u].v[t], mmax);
+                        og |= !(on_grid(tail[u].x, mmax) && on_grid(tail[u].y, mmax) && on_grid(tail[u].z, mmax) &&
+                                on_grid(tail[u].w, mmax));
                     }
                 }
             } else {
 #pragma unroll
                 for (int u = 0; u < kPtBatch; ++u) {
                     const int i = i0 + u * kPtThreads;
-                    if (i < np)
-                        copy_row(h.emb + (e.pt_off + first + i) * D, reinterpret_cast<float4*>(st.xs + pos[u] * dp), D,
-                                 dp, vec);
+                    if (i < np) {
+                        const float* x = h.emb + (e.pt_off + first + i) * D;
+                        copy_row(x, reinterpret_cast<float4*>(st.xs + pos[u] * dp), D, dp, vec);
+                        for (int t = 0; t < D; ++t) og |= !on_grid(__ldg(x + t), mmax);
+                    }
                 }
             }
 #pragma unroll
@@ -1057,6 +1082,7 @@ __global__ void __launch_bounds__(kPtThreads) k_scatter(DevState st)
             }
         }
     }
+    if (__syncthreads_or(og) && threadIdx.x == 0) atomicOr(st.offgrid, 1u);
 }
 
 // Stage 4b: the filter key of every point, in cell order (FiltPlan), from
@@ -1111,6 +1137,13 @@ __device__ __forceinline__ unsigned long long pk_sqr(unsigned long long d)
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(0ull));
     return r;
 }
+// s + d * d on each half with one rounding (the exact fast path only).
+__device__ __forceinline__ unsigned long long pk_fma(unsigned long long d, unsigned long long s)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(s));
+    return r;
+}
 __device__ __forceinline__ unsigned long long pk_add(unsigned long long a, unsigned long long b)
 {
     unsigned long long r;
@@ -1145,17 +1178,24 @@ __device__ __forceinline__ void load_cand(const float4* row, CandPk<DP4>& cp)
 
 // d2 of the query pair stored at qp (dims interleaved: q0[t], q1[t]) against
 // the lane's candidate.  Low half: first query of the pair.
-template <int DP4>
+// FMA: every point of the call is on the exact fast path's grid (on_grid),
+// so each square is added with one fused multiply-add, same bits.
+template <int DP4, bool FMA = false>
 __device__ __forceinline__ float2 dist2_pair(const ulonglong2* qp, const CandPk<DP4>& cp)
 {
     unsigned long long s = 0ull;
 #pragma unroll
     for (int k = 0; k < 2 * DP4; ++k) {
         const ulonglong2 q = qp[k];  // dims 2k and 2k+1 of both queries
-        unsigned long long d = pk_sub(q.x, cp.c[2 * k]);
-        s = pk_add(s, pk_sqr(d));
-        d = pk_sub(q.y, cp.c[2 * k + 1]);
-        s = pk_add(s, pk_sqr(d));
+        if constexpr (FMA) {
+            s = pk_fma(pk_sub(q.x, cp.c[2 * k]), s);
+            s = pk_fma(pk_sub(q.y, cp.c[2 * k + 1]), s);
+        } else {
+            unsigned long long d = pk_sub(q.x, cp.c[2 * k]);
+            s = pk_add(s, pk_sqr(d));
+            d = pk_sub(q.y, cp.c[2 * k + 1]);
+            s = pk_add(s, pk_sqr(d));
+        }
     }
     return make_float2(__uint_as_float((unsigned)s), __uint_as_float((unsigned)(s >> 32)));
 }
@@ -1661,10 +1701,12 @@ __device__ __forceinline__ void park_rows(const DevState& st, unsigned long long
 // Stage 5: count every query's neighbours; rows of at most kFast neighbours
 // are also collected, sorted, cut at k and written to the pool (space taken
 // per chunk from a counter), so that stage 7 only copies them.
-template <int DP4>
+// Launched twice per build, FMA = false and true: the instance that does not
+// match the scatter's grid flag returns at once.
+template <int DP4, bool FMA>
 __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2) k_walk_collect(DevState st)
 {
-    if (timed_out(st)) return;
+    if (timed_out(st) || (__ldcg(st.offgrid) == 0u) != FMA) return;
     extern __shared__ float4 s_dyn[];
     constexpr int DP = 4 * DP4;
     const int lane = threadIdx.x & 31;
@@ -1739,7 +1781,7 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
                         // here and taken out below, which keeps a self test out of this loop.
         #pragma unroll 2
                         for (int pp = p0; pp < p1; ++pp) {
-                            const float2 d = dist2_pair<DP4>(sqp + pp * 2 * DP4, cp);
+                            const float2 d = dist2_pair<DP4, FMA>(sqp + pp * 2 * DP4, cp);
                             const int i0 = 2 * pp, i1 = 2 * pp + 1;
                             const bool h0 = cv && (i0 >= a) && d.x <= r2;
                             const bool h1 = cv && (i1 < e) && d.y <= r2;
@@ -2894,6 +2936,15 @@ int emit_smem(int cap)
     return (kFillThreads / 32) * (2 * 4 * DP4 * (int)sizeof(float) + 2 * cap * (int)sizeof(unsigned long long));
 }
 
+// The candidate-major collect walk: both instances, one of which returns at
+// once (k_walk_collect).
+template <int DP4>
+void launch_collect(const DevState& st, const LaunchCfg& cfg, cudaStream_t s)
+{
+    k_walk_collect<DP4, false><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+    k_walk_collect<DP4, true><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+}
+
 template <int DP4>
 cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, int walk, cudaStream_t s, cudaEvent_t* ev)
 {
@@ -2902,9 +2953,9 @@ cudaError_t launch_walks(const DevState& st, const LaunchCfg& cfg, int walk, cud
         if (walk == kWalkQueryMajor)
             k_walk_collect_q<DP4><<<cfg.grid_count_q, kWalkThreads, collect_q_smem<DP4>(), s>>>(st);
         else
-            k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+            launch_collect<DP4>(st, cfg, s);
     } else {
-        k_walk_collect<DP4><<<cfg.grid_count, kWalkThreads, collect_smem<DP4>(), s>>>(st);
+        launch_collect<DP4>(st, cfg, s);
     }
     mark(ev, 5, s);
     k_scan<1><<<cfg.grid_scan, kScanThreads, 0, s>>>(st);
@@ -2923,14 +2974,16 @@ cudaError_t config_walks(int fill_cap, int n_sm, LaunchCfg* cfg)
     // The attribute is a per-kernel upper bound shared by every plan in the
     // process, so it is set to the largest size any cap (k <= 1024) can need,
     // never lowered to this plan's size.
-    cudaError_t e = cudaFuncSetAttribute(k_walk_collect<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_collect<DP4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_walk_collect<DP4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, csm);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_walk_emit<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_walk_knn<DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, emit_smem<DP4>(2048));
     if (e != cudaSuccess) return e;
     int nb_c = 0, nb_f = 0, nb_q = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4>, kWalkThreads, csm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_c, k_walk_collect<DP4, false>, kWalkThreads, csm);
     if (e != cudaSuccess) return e;
     if constexpr (DP4 <= 3) {
         const int qsm = collect_q_smem<DP4>();

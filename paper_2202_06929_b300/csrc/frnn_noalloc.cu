@@ -53,7 +53,8 @@ constexpr size_t kOffCellsTotal = align256(kOffCounters + sizeof(unsigned) * kCt
 constexpr size_t kOffPoolCtr = align256(kOffCellsTotal + sizeof(int));
 constexpr size_t kOffEdgeOff = align256(kOffPoolCtr + sizeof(unsigned long long));
 constexpr size_t kOffStatus = align256(kOffEdgeOff + 2 * sizeof(int));
-constexpr size_t kOffKey = align256(kOffStatus + sizeof(unsigned));
+constexpr size_t kOffOffgrid = align256(kOffStatus + sizeof(unsigned));
+constexpr size_t kOffKey = align256(kOffOffgrid + sizeof(unsigned));
 constexpr size_t kOffRank = align256(kOffKey + sizeof(unsigned) * kNoallocMaxPoints);
 constexpr size_t kOffPerm = align256(kOffRank + sizeof(unsigned) * kNoallocMaxPoints);
 constexpr size_t kOffCellS = align256(kOffPerm + sizeof(int) * kNoallocMaxPoints);
@@ -204,6 +205,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
     st.pool_ctr = reinterpret_cast<unsigned long long*>(b + kOffPoolCtr);
     st.edge_off = reinterpret_cast<int*>(b + kOffEdgeOff);
     st.status = reinterpret_cast<unsigned*>(b + kOffStatus);
+    st.offgrid = reinterpret_cast<unsigned*>(b + kOffOffgrid);
 
     // Everything that must start at zero (or at the empty bounding box) is
     // cleared here, on the caller's stream, before the build runs.
