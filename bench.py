@@ -55,9 +55,9 @@ AUTOTUNE_SPACE = ("20 grids (g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}
 # collect walk, from one ncu capture of the N=120k workload (40 events, 4.8 M
 # points); valid only for the kernel code it was taken on (the sha1 of the
 # kernel file without comments) and the walk form it ran.
-MEASURED_COLLECT = {"workload": "c2", "stage": "walk_collect", "walk": 2, "source_sha1_prefix": "9a427fc76863",
-                    "bytes_per_point": (240_643_328 + 212_335_872) / 4_800_000,
-                    "instr_per_query": 1_008_753_193 / 4_800_000}
+MEASURED_COLLECT = {"workload": "c2", "stage": "walk_collect", "walk": 2, "source_sha1_prefix": "58048ec5ff23",
+                    "bytes_per_point": (240_604_160 + 212_458_240) / 4_800_000,
+                    "instr_per_query": 1_008_921_934 / 4_800_000}
 
 
 def parse_args(argv=None):
