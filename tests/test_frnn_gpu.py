@@ -2,8 +2,10 @@
 
 Every comparison is exact: row_ptr and col equal element by element (and d2
 bit for bit when emitted).  The CUDA path computes each squared distance with
-the same float32 operations in the same order as the oracle, so the edge sets
-agree on any input, on the 1/256 grid or off it.  Both forms of the
+the same float32 operations in the same order as the oracle (or, when every
+coordinate is on the 1/256 grid and every partial sum is exact, with fused
+multiply-adds that give the same bits), so the edge sets agree on any input,
+on the 1/256 grid or off it.  Both forms of the
 neighbour walk (candidates across the lanes, or a lane per query) are
 checked on the seeded sweep, the tunings and the full-size events.
 """
@@ -354,6 +356,39 @@ def test_batched_equals_each_event_alone(use_graph):
             np.testing.assert_array_equal(col, ocol)
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("off_grid_event", [None, 0, 2])
+def test_candidate_major_fused_and_exact_sums_on_one_plan(off_grid_event):
+    """The candidate-major walk adds squares with fused multiply-adds only
+    when every coordinate of the call is on the 1/256 grid (small enough that
+    every partial sum is exact); one event off the grid makes the whole call
+    take the sequential sum.  Builds of both kinds alternate on one plan (and
+    its captured graph), and every row equals the oracle's, d2 included."""
+    sizes = [3000, 1500, 2500]
+    evs = _events("cluster", sizes, 12, 400)
+    if off_grid_event is not None:
+        rng = np.random.default_rng(5)
+        x = evs[off_grid_event].astype(np.float64)
+        evs[off_grid_event] = (x + rng.uniform(-1e-3, 1e-3, size=x.shape)).astype(np.float32)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    allx = np.concatenate(evs).astype(np.float32)
+    grid = _events("grid", sizes, 12, 401)
+    gx = np.concatenate(grid).astype(np.float32)
+    with frnn.Plan(n_max=int(off[-1]), d_max=12, k_max_cap=24, events_max=4, emit_d2=True, use_graph=True) as plan:
+        plan.set_tuning(0, 0.0, frnn._native.FRNN_WALK_CANDIDATES)
+        for batch, xs_ in ((allx, evs), (gx, grid), (allx, evs)):
+            csr = plan.build_batched(torch.from_numpy(batch).cuda(), off, 0.15, 24)
+            host = csr.to_host()
+            assert plan.last_status() == 0
+            for b, x in enumerate(xs_):
+                rp, col = csr.event_rows(host, b)
+                orp, ocol, od2 = oracle.radius_graph(x, 0.15, 24, with_d2=True)
+                np.testing.assert_array_equal(rp, orp)
+                np.testing.assert_array_equal(col, ocol)
+                e0 = int(host["edge_off"][b])
+                d2 = host["d2"][e0:e0 + int(orp[-1])]
+                np.testing.assert_array_equal(d2.view(np.uint32), od2.view(np.uint32))
 
 
 def test_host_to_host_call_matches_device_call():
