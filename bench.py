@@ -319,7 +319,9 @@ def stage_bytes(n_total: int, n_edges: int, d: int, long_edges: int = 0, long_ro
         "bbox_plan": 4 * n_total * d,
         "key_hist": 4 * n_total * d + 8 * n_total,
         "scan_cells": 0,  # size of the cell table, reported separately
-        "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total,
+        # scatter (points moved, key and rank read, perm and cell id written)
+        # and filter keys (sorted rows read, one 4-byte key written)
+        "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total + 4 * n_total * dp + 4 * n_total,
         # sorted points read once; per point its cell id, count and pool slot; rows parked
         "walk_collect": 4 * n_total * dp + 4 * n_total + 8 * n_total + 4 * parked,
         # per point its count and pool slot read, row_ptr written; parked rows

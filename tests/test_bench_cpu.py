@@ -60,6 +60,8 @@ def test_stage_bytes_total_matches_whole_build_terms():
     b = bench.stage_bytes(1000, 5000, 8)
     assert b["walk_collect"] == 4 * 1000 * 8 + 12 * 1000 + 4 * 5000
     assert b["scan_rows"] == 12 * 1000 + 8 * 5000
+    # scatter stage: the scatter's moves and the filter keys read back from the sorted rows
+    assert b["scatter"] == (4 * 1000 * 8 + 16 * 1000 + 4 * 1000 * 8) + (4 * 1000 * 8 + 4 * 1000)
 
 
 def test_edge_feature_bytes_counts_outputs_columns_and_rows():
