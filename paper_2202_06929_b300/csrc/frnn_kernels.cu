@@ -2229,12 +2229,15 @@ __device__ __forceinline__ void emit_row_out(const DevState& st, unsigned long l
 // (distance j >= 32) are swapped in place, with the register pairs fixed at
 // compile time; partners in other lanes are exchanged by shuffles.  Only the
 // loop over registers is unrolled, which keeps the network's code small.
-template <int R>
+// KMAX < 32 R: only the stages k = 2 .. KMAX, so that every block of KMAX
+// keys ends sorted, ascending in even blocks and descending in odd ones.
+template <int R, int KMAX = 32 * R>
 __device__ __forceinline__ void reg_bitonic_sort(unsigned long long (&v)[R], int lane)
 {
-    for (int k = 2; k <= 32 * R; k <<= 1) {
+    constexpr int JR0 = R >= 16 ? 8 : R >= 8 ? 4 : R >= 4 ? 2 : 1;  // largest power of two <= R / 2
+    for (int k = 2; k <= KMAX; k <<= 1) {
 #pragma unroll
-        for (int jr = R / 2; jr >= 1; jr >>= 1) {
+        for (int jr = JR0; jr >= 1; jr >>= 1) {
             if ((jr << 5) < k) {  // distance 32 jr is one of this k's stages (k/2 down to 32)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
@@ -2302,6 +2305,83 @@ __device__ __forceinline__ void emit_spilled_keys(const DevState& st, const ulon
     }
 }
 
+// Bitonic merge of 128 keys in four registers (key e in lane e % 32, register
+// e / 32) that form a bitonic sequence: ascending (UP) or descending after.
+template <bool UP>
+__device__ __forceinline__ void reg_bitonic_merge128(unsigned long long (&m)[4], int lane)
+{
+#pragma unroll
+    for (int jr = 2; jr >= 1; jr >>= 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if ((r & jr) == 0) {
+                const unsigned long long a = m[r], b = m[r | jr];
+                const bool sw = (a > b) == UP;
+                m[r] = sw ? b : a;
+                m[r | jr] = sw ? a : b;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const unsigned long long o = __shfl_xor_sync(kFull, m[r], j);
+            m[r] = (lower == UP) ? (m[r] < o ? m[r] : o) : (m[r] < o ? o : m[r]);
+        }
+    }
+}
+
+// A kept row of 128 < hits <= 128 NB whose cap is at most 128: only its 128
+// smallest keys other than the query's own are sorted.  Each block of 128
+// keys is sorted (alternately ascending and descending), the elementwise
+// minimum of an ascending and a descending block holds the 128 smallest of
+// both as a bitonic sequence (a half-cleaner), and one merge of 128 sorts
+// them; a third block is folded in the same way.  The query's own key is
+// replaced by the largest key before sorting.
+template <int DP4, int NB>
+__device__ __forceinline__ void emit_spilled_top128(const DevState& st, const ulonglong2 (&qv)[DP4], long long at,
+                                                    int raw, int rs, int cnt, unsigned self_j, int lane)
+{
+    constexpr int R = 4 * NB;
+    const ulonglong2* xs2 = reinterpret_cast<const ulonglong2*>(st.xs);
+    const unsigned long long self_key = (unsigned long long)self_j;
+    unsigned long long v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = (r << 5) | lane;
+        v[r] = ~0ull;
+        if (e < raw) {
+            const int pos = __ldg(st.spill + at + e);
+            ulonglong2 cv[DP4];
+#pragma unroll
+            for (int k = 0; k < DP4; ++k) cv[k] = __ldg(xs2 + (long long)pos * DP4 + k);
+            const unsigned long long key = edge_key(dist2_rows<DP4>(qv, cv), __ldg(st.perm + pos));
+            v[r] = key == self_key ? ~0ull : key;
+        }
+    }
+    reg_bitonic_sort<R, 128>(v, lane);
+    unsigned long long m[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) m[r] = v[r] < v[4 + r] ? v[r] : v[4 + r];
+    if constexpr (NB == 3) {
+        reg_bitonic_merge128<false>(m, lane);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) m[r] = m[r] < v[8 + r] ? m[r] : v[8 + r];
+    }
+    reg_bitonic_merge128<true>(m, lane);
+    const int emit = st.hdr->emit_d2;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = (r << 5) | lane;
+        if (e < cnt) {
+            st.col[rs + e] = (int)(unsigned)m[r];
+            if (emit) st.d2[rs + e] = __uint_as_float((unsigned)(m[r] >> 32));
+        }
+    }
+}
+
 // A long row whose hits the collect walk kept (list entry li, query at
 // sorted position q): each hit's d2 is computed again with the walk's
 // arithmetic, the keys (d2, j) are sorted in registers, and the smallest
@@ -2332,8 +2412,16 @@ __device__ void emit_spilled_row(const DevState& st, long long q, int li, unsign
             emit_spilled_keys<DP4, 4>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
             return;
         }
+        if (cnt <= 128 && raw <= 256) {
+            emit_spilled_top128<DP4, 2>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
+            return;
+        }
         if (raw <= 256) {
             emit_spilled_keys<DP4, 8>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
+            return;
+        }
+        if (cnt <= 128 && raw <= 384) {
+            emit_spilled_top128<DP4, 3>(st, qv, at, raw, rs, cnt, (unsigned)self_j, lane);
             return;
         }
         // more keys than the registers hold: sorted in the warp's buffer
@@ -2374,9 +2462,10 @@ __device__ void emit_spilled_row(const DevState& st, long long q, int li, unsign
 // Stage 7a: the long rows whose hits the collect walk kept, a warp per row
 // taken from a counter (a kernel of its own: its code stays small).  buf:
 // per warp 2 x kSpillSlots keys of dynamic shared memory for rows with more
-// than 256 hits.
+// than 256 hits and a cap above 128.  Seven blocks per SM: the twelve-register
+// sorting network of the top-128 path fits without spills.
 template <int DP4>
-__global__ void __launch_bounds__(kFillThreads, 8) k_emit_kept(DevState st)
+__global__ void __launch_bounds__(kFillThreads, 7) k_emit_kept(DevState st)
 {
     if (timed_out(st) || !st.spill_at) return;
     extern __shared__ unsigned long long s_kept[];
