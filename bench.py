@@ -55,9 +55,9 @@ AUTOTUNE_SPACE = ("20 grids (g_max in {6,5,4,3,2} x cell_scale in {1,1.25,1.5,2}
 # collect walk, from one ncu capture of the N=120k workload (40 events, 4.8 M
 # points); valid only for the kernel code it was taken on (the sha1 of the
 # kernel file without comments) and the walk form it ran.
-MEASURED_COLLECT = {"workload": "c2", "stage": "walk_collect", "walk": 2, "source_sha1_prefix": "58048ec5ff23",
-                    "bytes_per_point": (240_604_160 + 212_458_240) / 4_800_000,
-                    "instr_per_query": 1_008_921_934 / 4_800_000}
+MEASURED_COLLECT = {"workload": "c2", "stage": "walk_collect", "walk": 2, "source_sha1_prefix": "92bbb52820ee",
+                    "bytes_per_point": (240_564_224 + 212_406_784) / 4_800_000,
+                    "instr_per_query": 1_008_893_392 / 4_800_000}
 
 
 def parse_args(argv=None):
@@ -799,7 +799,8 @@ def main(argv=None):
     clocks = clk.summary()
     # ---- arithmetic view of the walks: candidate distance tests per step
     # (every query against its candidates in the collect walk, and the long
-    # rows once more in the emit walk), FP32 operations 3 D per test (one
+    # rows once more in the emit walk unless the plan keeps their hits, whose
+    # recomputed distances are not counted), FP32 operations 3 D per test (one
     # subtraction, one product, one addition per dim), against the FP32 rate
     # derived from the SM count, 128 FP32 lanes per SM, two operations per
     # lane per packed f32x2 instruction, and the maximum SM clock
@@ -809,7 +810,8 @@ def main(argv=None):
         g_used, s_used, _ = plan.get_tuning()
         mean_cand, g_grid = host_candidates(x_host[off[0]:off[1]], r, g_used, s_used, cpp)
         long_frac = float(np.mean(long_mask))
-        evals = mean_cand * n_total * (1.0 + long_frac)
+        kept = hits(n_total) > 0 and walk_used == 1  # the candidate-major walk keeps long rows' hits
+        evals = mean_cand * n_total * (1.0 + (0.0 if kept else long_frac))
         ops = evals * 3 * d
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_tops = n_sm * 128 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks["sm_max_mhz"] else None
@@ -824,7 +826,7 @@ def main(argv=None):
                      "note": "instructions per query from the ncu capture of the same kernel code, scaled to this "
                              "launch; peak = 4 warp instructions per cycle per SM x SMs x max SM clock"}
         alu = {"candidate_tests_per_step": evals, "mean_candidates_per_query": mean_cand,
-               "gridded_dims": g_grid, "long_row_fraction": long_frac,
+               "gridded_dims": g_grid, "long_row_fraction": long_frac, "long_rows_walked_again": not kept,
                "candidate_tests_per_s": evals / (total_ms_max / args.steps / 1e3),
                "fp32_ops_per_test": 3 * d, "achieved_tops": achieved_tops, "peak_tops_derived": peak_tops,
                "frac": achieved_tops / peak_tops if peak_tops else None,
