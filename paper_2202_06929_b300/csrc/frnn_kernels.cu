@@ -1841,10 +1841,11 @@ __global__ void __launch_bounds__(kWalkThreads, DP4 <= 2 ? 7 : DP4 <= 4 ? 6 : 2)
 
 constexpr int kRunCap = 256;  // run-list entries per warp
 static_assert(kRunCap >= kMaxRuns, "the runs of any one segment must fit the run list");
-// Rows of this form hold up to 20 neighbours (longer ones go to the emit
-// walk): with 21 slots a warp's shared memory leaves room for 7 blocks of 4
-// warps per SM, as its registers do.  The stride is odd, so the rows of
-// lanes 0..15 start in distinct banks.
+// Rows of this form hold up to 21 filter passes, the query itself among
+// them (a row with more goes to the emit walk); after the exact test they
+// hold the keys of up to 20 neighbours.  With 21 slots a warp's shared
+// memory leaves room for 7 blocks of 4 warps per SM, as its registers do.
+// The stride is odd, so the rows of lanes 0..15 start in distinct banks.
 constexpr int kRowSlotsQ = 21;
 constexpr int kRowStrideQ = 21;
 // 8-byte words of shared memory per warp: rows, run list, segment bounds
