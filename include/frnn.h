@@ -55,7 +55,9 @@ typedef enum {
     FRNN_ERR_NONFINITE_INPUT = 4, /* an event holds NaN or Inf; its rows are left empty */
     FRNN_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                 */
     FRNN_ERR_OVERFLOW = 6,        /* the edges did not fit the plan's edge capacity     */
-    FRNN_ERR_CAPACITY = 7         /* the call exceeds a capacity fixed at plan creation */
+    FRNN_ERR_CAPACITY = 7,        /* the call exceeds a capacity fixed at plan creation */
+    FRNN_ERR_CHECK = 8            /* a debug check of a build's output failed (FRNN_DEBUG,
+                                     frnn_check_last_build): a defect of the library    */
 } frnn_status;
 
 /* k_max value that keeps every row whole: the paper's own FRNN list (Sec. 3.4,
@@ -69,6 +71,8 @@ typedef enum {
 #define FRNN_USE_GRAPH 0x2u  /* replay the build as a CUDA graph captured on first use */
 #define FRNN_AUTOTUNE 0x4u   /* a radius build whose call shape has no autotuned entry
                                 yet runs frnn_plan_autotune first (synchronously)      */
+#define FRNN_DEBUG 0x8u      /* every build (radius or kNN) is followed on its stream by
+                                frnn_check_last_build (slow: a brute-force pass)       */
 
 typedef struct frnn_plan frnn_plan; /* opaque; owns all device scratch and outputs */
 
@@ -80,7 +84,7 @@ typedef struct {
     int k_max_cap;         /* largest neighbour cap of one call, 1..1024              */
     int64_t edge_capacity; /* col slots; 0 = n_max * k_max_cap (never overflows)      */
     int cells_per_point;   /* cell-table slots per point (plus 4096 per event); 0 = 4 */
-    uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH | FRNN_AUTOTUNE           */
+    uint32_t flags;        /* FRNN_EMIT_D2 | FRNN_USE_GRAPH | FRNN_AUTOTUNE | FRNN_DEBUG */
     int64_t hit_capacity;  /* 4-byte slots in which the neighbour walk keeps every
                               neighbour of rows longer than 24 (384 per row, taken 32
                               rows at a time), so that their k nearest are sorted from
@@ -298,8 +302,9 @@ FRNN_API int frnn_knn_graph_batched(frnn_plan* plan, const float* emb, const int
 /*
  * Synchronise `stream`, then return and clear the status latched by the
  * plan's kernels since the last call (FRNN_OK if none).  If several errors
- * were latched the most severe is returned, in the order TIMEOUT, OVERFLOW,
- * NONFINITE_INPUT.  A CUDA error on the stream returns FRNN_ERR_CUDA.
+ * were latched the most severe is returned, in the order CHECK, TIMEOUT,
+ * OVERFLOW, NONFINITE_INPUT.  A CUDA error on the stream returns
+ * FRNN_ERR_CUDA.
  *
  * TIMEOUT: one of the scans' waits for a preceding tile (each bounded to
  * 2^22 polls and 1 s) ran out, so cell or row offsets of that build may be
@@ -314,6 +319,71 @@ FRNN_API int frnn_knn_graph_batched(frnn_plan* plan, const float* emb, const int
  * until the next build).
  */
 FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
+
+/*
+ * Debug checks of the plan's last build (radius or kNN), enqueued on `stream`
+ * as kernels that only read the build's buffers and the caller's input, which
+ * must be unchanged since the build; run them before frnn_label_components,
+ * which reuses scratch the checks read.  Each check tests one stage's output
+ * against what that stage must produce (Sec. 3.4: cell lists, then per-point
+ * neighbour lists), in pipeline order:
+ *   FRNN_CHECK_EVENT_OFFSETS  edge_off[b] = row_ptr[first point of b], and
+ *                             edge_off[n_events] = row_ptr[n_total]
+ *   FRNN_CHECK_CELL_TABLE     an event's cell offsets ascend from its first
+ *                             sorted position to one past its last
+ *   FRNN_CHECK_SCATTER        the sorted order is a permutation of each
+ *                             event's points, each inside its cell's range,
+ *                             its sorted row the input row bit for bit
+ *   FRNN_CHECK_ROW_PTR        row_ptr[0] = 0, rows do not shrink, no row
+ *                             exceeds the cap; rows of an event with NaN/Inf
+ *                             are empty (radius) or min(k, n_b - 1) long (kNN)
+ *   FRNN_CHECK_COLUMN         each column is an index of the event other than
+ *                             the row's own (kNN, NaN/Inf event: -1)
+ *   FRNN_CHECK_RADIUS         d2(i, j) <= fl32(r * r) (radius builds)
+ *   FRNN_CHECK_D2             the emitted d2 equals d2(i, j) bit for bit
+ *                             (plans with FRNN_EMIT_D2)
+ *   FRNN_CHECK_ORDER          sorted rows ascend strictly by (d2, j) (every
+ *                             row but the unsorted ones of FRNN_NO_CAP)
+ *   FRNN_CHECK_COMPLETE       brute force over the event: a row holds
+ *                             min(k, |S_i|) entries (kNN: min(k, n_b - 1)),
+ *                             no other point of the event is smaller by
+ *                             (d2, j) than its last, and the sums of its
+ *                             columns and their squares match the points that
+ *                             belong in it.  In an event of n_b > 2^17 points
+ *                             only every ceil(n_b^2 / 2^34)-th row is checked,
+ *                             so that no event costs more than 2^34 distances.
+ * d2 is recomputed as defined at the top of this file.  Checks 5-9 are
+ * skipped when the edges overflowed the edge capacity, and every check when a
+ * bounded wait of the build ran out (its rows are empty by design).  A failed
+ * check latches FRNN_ERR_CHECK (reported by frnn_get_last_status ahead of the
+ * other statuses) and is recorded for frnn_get_last_check.  Cost: on a B300
+ * the brute-force pass makes about 5 x 10^11 distance evaluations a second
+ * (d = 8; a 64-event batch of 120k-point events takes about 2 s).  No check
+ * traps or faults: every index read from the build's buffers is range-checked
+ * before it addresses memory.  Errors: INVALID_ARG (NULL plan, no build yet),
+ * CUDA.
+ */
+#define FRNN_CHECK_NONE 0
+#define FRNN_CHECK_EVENT_OFFSETS 1 /* index: event                          */
+#define FRNN_CHECK_CELL_TABLE 2    /* index: cell slot of the call's table  */
+#define FRNN_CHECK_SCATTER 3       /* index: sorted position                */
+#define FRNN_CHECK_ROW_PTR 4       /* index: point of the call              */
+#define FRNN_CHECK_COLUMN 5        /* index: edge of the call               */
+#define FRNN_CHECK_RADIUS 6        /* index: edge                           */
+#define FRNN_CHECK_D2 7            /* index: edge                           */
+#define FRNN_CHECK_ORDER 8         /* index: edge                           */
+#define FRNN_CHECK_COMPLETE 9      /* index: point                          */
+FRNN_API int frnn_check_last_build(frnn_plan* plan, void* stream);
+
+/*
+ * Synchronise `stream`, then return the first failure the debug checks have
+ * recorded since the last call, and clear the record: *check receives the
+ * FRNN_CHECK_* id of the earliest failing stage (FRNN_CHECK_NONE if none) and
+ * *index its smallest failing index of that check (-1 if none).  The status
+ * bit FRNN_ERR_CHECK is read and cleared by frnn_get_last_status.  Errors:
+ * INVALID_ARG (NULL argument), CUDA.
+ */
+FRNN_API int frnn_get_last_check(frnn_plan* plan, void* stream, int* check, int64_t* index);
 
 /*
  * Failure-detection test hook.  The next build that launches kernels on

@@ -22,11 +22,17 @@ FRNN_ERR_NONFINITE_INPUT = 4
 FRNN_ERR_TIMEOUT = 5
 FRNN_ERR_OVERFLOW = 6
 FRNN_ERR_CAPACITY = 7
+FRNN_ERR_CHECK = 8
 
 FRNN_NO_CAP = 0   # k = FRNN_NO_CAP keeps every row whole (rows over 32 neighbours unsorted)
 FRNN_EMIT_D2 = 0x1
 FRNN_USE_GRAPH = 0x2
 FRNN_AUTOTUNE = 0x4
+FRNN_DEBUG = 0x8
+
+# Debug checks of a build's output (frnn_check_last_build), in pipeline order.
+CHECKS = ("none", "event_offsets", "cell_table", "scatter", "row_ptr", "column", "radius", "d2", "order",
+          "complete")
 
 # Every function the header declares (checked by the tests against the .so).
 ABI_FUNCTIONS = (
@@ -37,6 +43,7 @@ ABI_FUNCTIONS = (
     "frnn_server_wait", "frnn_server_run_trace", "frnn_server_destroy", "frnn_plan_autotune",
     "frnn_label_components", "frnn_edge_features", "frnn_knn_graph_batched",
     "frnn_plan_test_stall_next_build", "frnn_server_poll", "frnn_server_get_stats", "frnn_plan_tuning_for",
+    "frnn_check_last_build", "frnn_get_last_check",
 )
 
 
@@ -120,6 +127,8 @@ def load():
     lib.frnn_edge_features.argtypes = [vp, vp, i64, i64, vp, vp]
     lib.frnn_get_last_status.argtypes = [vp, vp]
     lib.frnn_plan_test_stall_next_build.argtypes = [vp]
+    lib.frnn_check_last_build.argtypes = [vp, vp]
+    lib.frnn_get_last_check.argtypes = [vp, vp, P(ctypes.c_int), P(ctypes.c_int64)]
     lib.frnn_status_string.argtypes = [i32]
     lib.frnn_status_string.restype = ctypes.c_char_p
     lib.frnn_version.argtypes = []
@@ -236,13 +245,14 @@ class Plan:
 
     def __init__(self, n_max: int, d_max: int, k_max_cap: int, events_max: int = 1,
                  edge_capacity: int = 0, cells_per_point: int = 0, emit_d2: bool = False,
-                 use_graph: bool = False, device: int = 0, autotune: bool = False, hit_capacity: int = 0):
+                 use_graph: bool = False, device: int = 0, autotune: bool = False, hit_capacity: int = 0,
+                 debug: bool = False):
         lib = load()
         prm = frnn_plan_params(device=device, d_max=d_max, n_max=n_max, events_max=events_max,
                                k_max_cap=k_max_cap, edge_capacity=edge_capacity,
                                cells_per_point=cells_per_point, hit_capacity=hit_capacity,
                                flags=((FRNN_EMIT_D2 if emit_d2 else 0) | (FRNN_USE_GRAPH if use_graph else 0)
-                                      | (FRNN_AUTOTUNE if autotune else 0)))
+                                      | (FRNN_AUTOTUNE if autotune else 0) | (FRNN_DEBUG if debug else 0)))
         h = ctypes.c_void_p()
         _check(lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)), "frnn_plan_create")
         self._h = h
@@ -411,6 +421,19 @@ class Plan:
 
     def check(self, stream=None) -> None:
         _check(self.last_status(stream), "device status")
+
+    def check_last_build(self, stream=None) -> None:
+        """frnn_check_last_build: enqueue the debug checks of the last build
+        (a failure latches FRNN_ERR_CHECK; see last_check)."""
+        _check(load().frnn_check_last_build(self._h, _stream_handle(stream)), "frnn_check_last_build")
+
+    def last_check(self, stream=None) -> tuple[str, int]:
+        """frnn_get_last_check: synchronise, return (check name, index) of the
+        first recorded failure (("none", -1) if none) and clear the record."""
+        cid, idx = ctypes.c_int(0), ctypes.c_int64(0)
+        _check(load().frnn_get_last_check(self._h, _stream_handle(stream), ctypes.byref(cid), ctypes.byref(idx)),
+               "frnn_get_last_check")
+        return CHECKS[cid.value], int(idx.value)
 
     def test_stall_next_build(self) -> None:
         """frnn_plan_test_stall_next_build: the next build's scan waits run out

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfrnn.so")
-SOURCES = ["frnn_kernels.cu", "frnn_label.cu", "frnn_api.cu", "frnn_noalloc.cu", "frnn_server.cu"]
+SOURCES = ["frnn_kernels.cu", "frnn_label.cu", "frnn_debug.cu", "frnn_api.cu", "frnn_noalloc.cu", "frnn_server.cu"]
 HEADERS = [os.path.join(CSRC, "frnn_internal.h"), os.path.join(INCLUDE, "frnn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,6 +17,7 @@ using namespace frnn;
 namespace {
 
 constexpr int kRing = 4;  // pinned staging slots for the per-call header
+constexpr int kMaxAllocs = 48;  // device allocations of a plan, at most
 constexpr int kVersion = 10000;
 
 struct DeviceGuard {
@@ -97,7 +98,7 @@ struct frnn_plan {
     cudaEvent_t ring_ev[kRing] = {};
     int ring_pos = 0;
     // allocations to free
-    void* allocs[40] = {};
+    void* allocs[kMaxAllocs] = {};
     int n_allocs = 0;
     // graph cache (FRNN_USE_GRAPH)
     cudaStream_t cap_stream = nullptr;
@@ -114,6 +115,10 @@ struct frnn_plan {
     int last_d = 0;
     bool has_last = false;
     bool stall_next = false;  // frnn_plan_test_stall_next_build
+    // debug checks: first failure (check id << 48 | index, ~0 if none) and
+    // one bit per point of scratch
+    unsigned long long* chk_first = nullptr;
+    unsigned* chk_bits = nullptr;
     // autotuner: probe output (device, 3 x u64) and the tunings it found,
     // keyed by the shape of the call
     unsigned long long* probe = nullptr;
@@ -158,6 +163,7 @@ int plan_alloc(frnn_plan* p, T** out, long long count)
 {
     *out = nullptr;
     if (count <= 0) count = 1;
+    if (p->n_allocs >= kMaxAllocs) return FRNN_ERR_OOM;
     void* ptr = nullptr;
     if (cudaMalloc(&ptr, (size_t)count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
@@ -303,6 +309,15 @@ int check_build_args(const frnn_plan* p, const float* emb, const int64_t* ev_off
 int autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, float r, int k,
              cudaStream_t s, frnn_tuning* best, float* best_ms);
 
+// The debug checks of the plan's last build (p->last), on stream s.
+int run_checks(frnn_plan* p, cudaStream_t s)
+{
+    if (p->last.n_total == 0) return FRNN_OK;
+    return launch_checks(p->st, p->chk_first, p->chk_bits, p->last.n_total, p->last.n_events, p->cells_max,
+                         p->last_d, p->n_sm, s) == 0
+               ? FRNN_OK : FRNN_ERR_CUDA;
+}
+
 // One radius build, or with probe_out set the autotuner's probe of the grid
 // (stages 1-3 and the candidate count; the outputs are not written).
 int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d,
@@ -393,6 +408,8 @@ int build_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_e
     p->last_r2 = r * r;
     p->last_d = d;
     p->has_last = true;
+    // the autotuner's timed builds are not checked
+    if ((p->prm.flags & FRNN_DEBUG) && !p->tuning_fixed) return run_checks(p, s);
     return FRNN_OK;
 }
 
@@ -435,6 +452,7 @@ unsigned long long plan_device_bytes(const frnn_plan_params& q, long long cells_
     b += sizeof(int) * ec * 2 + (d2 ? 2 * sizeof(float) * ec : 0);
     b += 8 + sizeof(int) * (ev + 1) + 4 + sizeof(unsigned);
     b += 3 * sizeof(unsigned long long);  // autotuner probe
+    b += sizeof(unsigned long long) + sizeof(unsigned) * ((n + 31) / 32 + 1);  // debug checks
     b += sizeof(float) * n * (unsigned long long)q.d_max;  // input of the host-to-host call
     if (q.hit_capacity > 0)  // neighbours of long rows, and per long row its entry
         b += sizeof(int) * (unsigned long long)q.hit_capacity + 8 + (sizeof(long long) + sizeof(int)) * n;
@@ -558,6 +576,7 @@ const char* frnn_status_string(int status)
         case FRNN_ERR_TIMEOUT: return "a bounded device-side wait ran out";
         case FRNN_ERR_OVERFLOW: return "edges exceed the edge capacity";
         case FRNN_ERR_CAPACITY: return "call exceeds a plan capacity";
+        case FRNN_ERR_CHECK: return "a debug check of the build's output failed";
         default: return "unknown status";
     }
 }
@@ -637,6 +656,8 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     ALLOC(st.status, 1);
     ALLOC(st.offgrid, 1);
     ALLOC(p->probe, 3);
+    ALLOC(p->chk_first, 1);
+    ALLOC(p->chk_bits, (n + 31) / 32 + 1);
     ALLOC(p->d_input, n * q.d_max);  // the device copy of frnn_build_graph_host's input
     p->d_input_floats = n * q.d_max;
     if (q.hit_capacity > 0) {
@@ -657,6 +678,8 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     if (rc == FRNN_OK) {
         rc = reset_device_state(p, nullptr);
         if (rc == FRNN_OK && cudaMemset(st.status, 0, sizeof(unsigned)) != cudaSuccess) rc = FRNN_ERR_CUDA;
+        if (rc == FRNN_OK && cudaMemset(p->chk_first, 0xff, sizeof(unsigned long long)) != cudaSuccess)
+            rc = FRNN_ERR_CUDA;
         if (rc == FRNN_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FRNN_ERR_CUDA;
     }
     if (rc != FRNN_OK) {
@@ -813,6 +836,7 @@ int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off
     p->last_r2 = inf;
     p->last_d = d;
     p->has_last = true;
+    if (p->prm.flags & FRNN_DEBUG) return run_checks(p, s);
     return FRNN_OK;
 }
 
@@ -897,9 +921,41 @@ int frnn_get_last_status(frnn_plan* p, void* stream)
     unsigned word = 0;
     const int rc = read_status_bits(p, stream, &word);
     if (rc != FRNN_OK) return rc;
+    if (word & kStCheck) return FRNN_ERR_CHECK;
     if (word & kStTimeout) return FRNN_ERR_TIMEOUT;
     if (word & kStOverflow) return FRNN_ERR_OVERFLOW;
     if (word & kStNonfinite) return FRNN_ERR_NONFINITE_INPUT;
+    return FRNN_OK;
+}
+
+int frnn_check_last_build(frnn_plan* p, void* stream)
+{
+    if (!p || !p->has_last) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    return run_checks(p, static_cast<cudaStream_t>(stream));
+}
+
+int frnn_get_last_check(frnn_plan* p, void* stream, int* check, int64_t* index)
+{
+    if (!p || !check || !index) return FRNN_ERR_INVALID_ARG;
+    DeviceGuard dg(p->prm.device);
+    if (!dg.ok) return FRNN_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long rec = ~0ull;
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpyAsync(&rec, p->chk_first, sizeof(rec), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(p->chk_first, 0xff, sizeof(rec), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FRNN_ERR_CUDA;
+    }
+    if (rec == ~0ull) {
+        *check = FRNN_CHECK_NONE;
+        *index = -1;
+    } else {
+        *check = (int)(rec >> 48);
+        *index = (int64_t)(rec & 0xffffffffffffull);
+    }
     return FRNN_OK;
 }
 

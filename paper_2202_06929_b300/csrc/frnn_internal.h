@@ -27,6 +27,7 @@ constexpr int kSpillSlots = 384;    // neighbour positions kept per long row in 
 constexpr unsigned kStNonfinite = 1u << 4;
 constexpr unsigned kStTimeout = 1u << 5;
 constexpr unsigned kStOverflow = 1u << 6;
+constexpr unsigned kStCheck = 1u << 8;  // a debug check of the build's output failed
 
 // Written by the host once per call and uploaded in front of the event table.
 struct CallHdr {
@@ -201,6 +202,14 @@ int config_pt(int n_sm, LaunchCfg* cfg);
 int launch_probe(const DevState& st, const LaunchCfg& cfg, unsigned long long* out, void* stream);
 // The k-nearest-neighbour build (no radius): grid, fixed-length rows, ring walk.
 int launch_knn(const DevState& st, int dp4, const LaunchCfg& cfg, void* stream);
+
+// Debug checks of the last build (frnn_debug.cu): kernels that only read the
+// build's buffers and its input; a failure sets kStCheck in the status word
+// and lowers *first to (check id << 48 | index).  bits: (n_max + 31) / 32
+// words of scratch, cleared here.  n_total, n_events, d: those of the last
+// build (nothing is checked for n_total = 0).  Returns 0 or 1 (a CUDA error).
+int launch_checks(const DevState& st, unsigned long long* first, unsigned* bits, long long n_total,
+                  int n_events, long long cells_max, int d, int n_sm, void* stream);
 
 // Synchronise the stream, then return in *bits and clear the status bits the
 // plan's kernels latched (kStNonfinite, kStTimeout, kStOverflow); after a

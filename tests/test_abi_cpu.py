@@ -33,8 +33,8 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_status_strings():
-    for s in range(8):
-        assert frnn.status_string(s)
+    for s in range(9):
+        assert frnn.status_string(s) != "unknown status"
     assert frnn.status_string(999) == "unknown status"
 
 
@@ -46,6 +46,9 @@ def test_null_plan_and_bad_params_rejected_on_host():
     assert lib.frnn_build_graph_batched(None, None, off, 1, 3, ctypes.c_float(0.1), 4, None, ctypes.byref(c)) == 1
     assert lib.frnn_get_last_status(None, None) == 1
     assert lib.frnn_plan_test_stall_next_build(None) == 1
+    assert lib.frnn_check_last_build(None, None) == 1
+    cid, idx = ctypes.c_int(0), ctypes.c_int64(0)
+    assert lib.frnn_get_last_check(None, None, ctypes.byref(cid), ctypes.byref(idx)) == 1
     assert lib.frnn_plan_destroy(None) == 0
     h = ctypes.c_void_p()
     assert lib.frnn_plan_create(ctypes.byref(h), None) == 1
