@@ -358,7 +358,9 @@ FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
  * check latches FRNN_ERR_CHECK (reported by frnn_get_last_status ahead of the
  * other statuses) and is recorded for frnn_get_last_check.  Cost: on a B300
  * the brute-force pass makes about 5 x 10^11 distance evaluations a second
- * (d = 8; a 64-event batch of 120k-point events takes about 2 s).  No check
+ * (d = 8; a 64-event batch of 120k-point events takes about 2 s); on a single
+ * event large enough to be sampled it has few rows in flight and makes
+ * 1-3 x 10^11 a second.  No check
  * traps or faults: every index read from the build's buffers is range-checked
  * before it addresses memory.  Errors: INVALID_ARG (NULL plan, no build yet),
  * CUDA.

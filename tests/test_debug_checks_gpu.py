@@ -12,6 +12,8 @@ Two directions:
     word rewritten, in bounds) is reported by the check of the stage that
     owns that word, at that word's index, and the next build checks clean.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -142,6 +144,40 @@ def test_large_event_sampled_rows():
     x = synth.make_event("c4", 0, n=200_000)
     with frnn.Plan(n_max=len(x), d_max=8, k_max_cap=256, debug=True) as plan:
         _build(plan, [x], 0.1, 256)
+        _clean(plan)
+
+
+@functools.lru_cache(maxsize=1)
+def _workload_batch(name, n_ev):
+    evs = [synth.make_event(name, e) for e in range(n_ev)]
+    off = np.concatenate([[0], np.cumsum([e.shape[0] for e in evs])]).astype(np.int64)
+    return np.concatenate(evs), off
+
+
+FULL = {
+    # name: (workload, events, plan keyword arguments)
+    "c2_bench_batch": ("c2", 64, dict(edge_capacity=64 * 120_000 * 64, cells_per_point=32, use_graph=True)),
+    "c3_batch": ("c3", 64, dict(use_graph=True)),
+    "c5": ("c5", 1, dict(cells_per_point=32, hit_capacity=32 * 384 * 31_251)),
+    "c5b": ("c5b", 1, dict(cells_per_point=32, hit_capacity=32 * 384 * 31_251)),
+}
+
+
+@pytest.mark.parametrize("walk", [_native.FRNN_WALK_CANDIDATES, _native.FRNN_WALK_QUERIES], ids=["cand", "query"])
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_workloads_pass_every_check(name, walk):
+    """The workloads at full size, in the bench's plan configurations: every
+    row of the 64-event N=120k batch and of the 64-event C3 batch checked by
+    brute force against its whole event, and the million-point C5 and C5b
+    events on every 59th row (each against all 10^6 points)."""
+    wl, n_ev, kw = FULL[name]
+    w = synth.WORKLOADS[wl]
+    x, off = _workload_batch(wl, n_ev)
+    with frnn.Plan(n_max=int(off[-1]), d_max=w.d, k_max_cap=w.k, events_max=n_ev, **kw) as plan:
+        plan.set_tuning(4, 1.0, walk)
+        plan.build_batched(torch.from_numpy(x).cuda(), off, w.r, w.k)
+        assert plan.last_status() == frnn.FRNN_OK
+        plan.check_last_build()
         _clean(plan)
 
 
