@@ -308,17 +308,20 @@ def measured_collect(stage: str, workload: str, walk: int):
     return m if sha.startswith(m["source_sha1_prefix"]) else None
 
 
-def stage_bytes(n_total: int, n_edges: int, d: int, long_edges: int = 0, long_rows: int = 0):
+def stage_bytes(n_total: int, n_edges: int, d: int, long_edges: int = 0, long_rows: int = 0, cells: int = 0):
     """Algorithmic bytes of each stage for a batch (each stage's unavoidable
     reads of its inputs and writes of its outputs, counted once).  long_edges
     / long_rows: the edges and rows of the rows longer than the collect walk
-    parks (the emit walk writes those)."""
+    parks (the emit walk writes those); cells: the cell-table slots of the
+    batch's grids."""
     dp = (d + 3) // 4 * 4
     parked = n_edges - long_edges
     return {
         "bbox_plan": 4 * n_total * d,
         "key_hist": 4 * n_total * d + 8 * n_total,
-        "scan_cells": 0,  # size of the cell table, reported separately
+        # per cell slot its count read, its start written, its count cleared
+        # for the next build
+        "scan_cells": 12 * cells,
         # scatter (points moved, key and rank read, perm and cell id written)
         # and filter keys (sorted rows read, one 4-byte key written)
         "scatter": 4 * n_total * d + 8 * n_total + 4 * n_total * dp + 8 * n_total + 4 * n_total * dp + 4 * n_total,
@@ -366,13 +369,11 @@ def measure_link(torch, dev, h2d_bytes: int, d2h_bytes: int, reps: int = 5):
             "note": "pinned copies of one step's input and result sizes, each direction alone and both at once"}
 
 
-def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point: int, sample: int = 100_000,
-                    seed: int = 3):
-    """Mean number of candidates a query of this event is tested against by
-    the walk (the points of the 3^g cells around its cell), recounted on the
-    host with the planning rule (widest dims first, cell edge
-    r * cell_scale * (1 + 2^-6), stop below 4 cells or over the cell budget),
-    over a random sample of queries."""
+def host_grid(x, r: float, g_max: int, cell_scale: float, cells_per_point: int):
+    """The cell grid of one event, restated on the host from the planning
+    rule (widest dims first, cell edge r * cell_scale * (1 + 2^-6), stop below
+    4 cells or over the event's cell budget): (lo, cell edge, gridded dims,
+    cells along each)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     n, dd = x.shape
     lo = x.min(0)
@@ -394,7 +395,27 @@ def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point:
         dims.append(t)
         ncs.append(nc)
         cells *= nc
-    ncs = np.array(ncs)
+    return lo, s, dims, np.array(ncs)
+
+
+def host_cell_slots(x, off, r: float, g_max: int, cell_scale: float, cells_per_point: int) -> int:
+    """Cell-table slots of a batch (the cell scan's items): the product of the
+    cells along the gridded dims of every event (one for an empty event)."""
+    tot = 0
+    for b in range(len(off) - 1):
+        xb = x[off[b]:off[b + 1]]
+        tot += int(np.prod(host_grid(xb, r, g_max, cell_scale, cells_per_point)[3])) if len(xb) else 1
+    return tot
+
+
+def host_candidates(x, r: float, g_max: int, cell_scale: float, cells_per_point: int, sample: int = 100_000,
+                    seed: int = 3):
+    """Mean number of candidates a query of this event is tested against by
+    the walk (the points of the 3^g cells around its cell), recounted on the
+    host over the grid of host_grid, over a random sample of queries."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n = x.shape[0]
+    lo, s, dims, ncs = host_grid(x, r, g_max, cell_scale, cells_per_point)
     inv_s = np.float32(1) / s
     k = np.minimum(((x[:, dims] - lo[dims]) * inv_s).astype(np.int64), ncs - 1)
     cid = np.ravel_multi_index(k.T, ncs)
@@ -728,7 +749,9 @@ def main(argv=None):
     row_len = np.diff(plan.build_batched(x_dev, off, r, k, stream=stream).to_host()["row_ptr"].astype(np.int64))
     torch.cuda.synchronize(dev)
     long_mask = row_len > KFAST_ROWS
-    sbytes = stage_bytes(n_total, n_edges, d, int(row_len[long_mask].sum()), int(long_mask.sum()))
+    g_tu, s_tu, _ = plan.get_tuning()
+    cell_slots = host_cell_slots(x_host, off, r, g_tu, s_tu, cpp)
+    sbytes = stage_bytes(n_total, n_edges, d, int(row_len[long_mask].sum()), int(long_mask.sum()), cell_slots)
     hbm_peak, peak_kind = measured_peaks()
     # the build's algorithmic bytes (read the points once, write the CSR once)
     whole_bytes = 4 * n_total * d + 4 * (n_total + 1) + 4 * n_edges
@@ -736,9 +759,13 @@ def main(argv=None):
     stages = {}
     for sname in STAGES:
         ms_ = stage_avg[sname]
-        gbs = sbytes[sname] / (ms_ / 1e3) / 1e9 if ms_ > 0 else None
+        gbs = sbytes[sname] / (ms_ / 1e3) / 1e9 if ms_ > 0 and sbytes[sname] > 0 else None
         stages[sname] = {"ms": ms_, "algorithmic_bytes": sbytes[sname], "achieved_gbs": gbs,
                          "frac": gbs / hbm_peak if gbs is not None else None}
+        if sname == "walk_emit" and sbytes[sname] == 0:
+            stages[sname]["note"] = ("no row of this batch is longer than the collect walk parks; the emit walk "
+                                     "only took the rows whose filter passes outnumbered their row slots, which "
+                                     "the host cannot count, so no fraction is given")
 
     # ---- e2e: host buffers in, host CSR out.  Main figure: the server's trace
     # call (frnn_server_run_trace) with every event of K steps present at t = 0:

@@ -56,8 +56,34 @@ def test_host_candidates_equal_direct_count():
         assert abs(got - want) < 1e-9
 
 
+def test_host_cell_slots_sum_each_events_grid():
+    # the grid rule restated here (widest dims first while each has >= 4 cells
+    # and the table stays within the budget), one slot for an empty event
+    def direct(x, r, g, cpp):
+        lo = x.min(0)
+        w = (x.max(0) - lo).astype(np.float32)
+        order = np.argsort(-w, kind="stable")
+        s = np.float32(r) * np.float32(1 + 1 / 64)
+        cells, used = 1, 0
+        for i in range(g):
+            nc = int(w[int(order[i])] / s) + 1
+            if used and (nc < 4 or cells * nc > cpp * x.shape[0] + 4096):
+                break
+            cells *= nc
+            used += 1
+        return cells
+    evs = [synth.clustered_grid(n, 8, 11 + n, max(n // 10, 1), 0.03) for n in (3000, 500, 40)]
+    evs.insert(1, np.zeros((0, 8), np.float32))
+    off = np.concatenate([[0], np.cumsum([len(e) for e in evs])])
+    x = np.concatenate(evs)
+    for g, cpp in ((2, 32), (4, 32), (6, 4)):
+        want = sum(direct(e, 0.1, g, cpp) if len(e) else 1 for e in evs)
+        assert bench.host_cell_slots(x, off, 0.1, g, 1.0, cpp) == want
+
+
 def test_stage_bytes_total_matches_whole_build_terms():
-    b = bench.stage_bytes(1000, 5000, 8)
+    b = bench.stage_bytes(1000, 5000, 8, cells=777)
+    assert b["scan_cells"] == 12 * 777
     assert b["walk_collect"] == 4 * 1000 * 8 + 12 * 1000 + 4 * 5000
     assert b["scan_rows"] == 12 * 1000 + 8 * 5000
     # scatter stage: the scatter's moves and the filter keys read back from the sorted rows
