@@ -78,7 +78,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-slots", type=int, default=3, help="server slots of the end-to-end measurement")
-    ap.add_argument("--e2e-batch", type=int, default=0, help="events per server batch (default: a quarter of a step)")
+    ap.add_argument("--e2e-batch", type=int, default=0, help="events per server batch (default: an eighth of a step)")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-requests", type=int, default=2000,
                     help="measured requests per offered load (plus 200 warm-up)")
@@ -777,7 +777,7 @@ def main(argv=None):
         xin = pinned_x.numpy()
         e2e_steps = max(3, min(args.steps, 10))
         sizes = np.diff(off)
-        per_batch = args.e2e_batch or max(1, B // 4)
+        per_batch = args.e2e_batch or max(1, B // 8)
         srv = frnn.Server(d=d, r=r, k=k, batch_points=int(per_batch * n_max_event), batch_events=per_batch,
                           slots=args.e2e_slots, edges_per_point=epp, device=local)
         try:

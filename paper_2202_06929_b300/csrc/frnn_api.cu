@@ -1015,13 +1015,31 @@ int frnn::read_status_bits(frnn_plan* p, void* stream, unsigned* bits)
         cudaGetLastError();
         return FRNN_ERR_CUDA;
     }
-    if (word & kStTimeout) {
-        // a wait gave up part-way: restore the between-builds state; the last
-        // graph is not valid, so labeling and edge features refuse it
-        reset_device_state(p, s);
-        cudaStreamSynchronize(s);
-        p->has_last = false;
-    }
+    if (word & kStTimeout) recover_after_timeout(p, stream);
     *bits = word;
     return FRNN_OK;
+}
+
+int frnn::enqueue_status_read(frnn_plan* p, void* stream, unsigned* h_word)
+{
+    DeviceGuard dg(p->prm.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(h_word, p->st.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(p->st.status, 0, sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return 0;
+}
+
+int frnn::recover_after_timeout(frnn_plan* p, void* stream)
+{
+    // a wait gave up part-way: restore the between-builds state; the last
+    // graph is not valid, so labeling and edge features refuse it
+    DeviceGuard dg(p->prm.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = reset_device_state(p, s);
+    const bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+    p->has_last = false;
+    return (rc == FRNN_OK && ok) ? FRNN_OK : FRNN_ERR_CUDA;
 }

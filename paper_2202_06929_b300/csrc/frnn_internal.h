@@ -217,4 +217,15 @@ int launch_checks(const DevState& st, unsigned long long* first, unsigned* bits,
 // frnn_get_last_status (frnn_api.cu).  Returns FRNN_OK or an error status.
 int read_status_bits(struct ::frnn_plan* p, void* stream, unsigned* bits);
 
+// Without a synchronisation: enqueue on the stream a copy of the plan's
+// status word into *h_word (pinned host memory), then its reset; the word is
+// valid once the stream has passed this point.  Returns 0 or 1 (a CUDA
+// error).  A word holding kStTimeout must be followed by
+// recover_after_timeout before the plan's next build.
+int enqueue_status_read(struct ::frnn_plan* p, void* stream, unsigned* h_word);
+
+// Restore the plan's between-builds state after a bounded wait ran out and
+// forget its last build, as frnn_get_last_status does (synchronous).
+int recover_after_timeout(struct ::frnn_plan* p, void* stream);
+
 }  // namespace frnn

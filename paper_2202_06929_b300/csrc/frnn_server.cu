@@ -82,6 +82,7 @@ struct Slot {
     int32_t* h_row_ptr = nullptr;          // pinned
     int32_t* h_edge_off = nullptr;         // pinned
     int32_t* h_col = nullptr;              // pinned
+    unsigned* h_status = nullptr;          // pinned: the plan's status word after the batch's build
     SlotState state = kIdle;
     std::vector<Request*> reqs;
     std::vector<int64_t> ev_off;
@@ -144,6 +145,7 @@ void free_slot(Slot& s)
     if (s.h_row_ptr) cudaFreeHost(s.h_row_ptr);
     if (s.h_edge_off) cudaFreeHost(s.h_edge_off);
     if (s.h_col) cudaFreeHost(s.h_col);
+    if (s.h_status) cudaFreeHost(s.h_status);
     s = Slot{};
 }
 
@@ -247,6 +249,8 @@ void launch_batch(frnn_server* srv, Slot& s)
                         s.stream);
         cudaMemcpyAsync(s.h_edge_off, s.csr.edge_off, sizeof(int32_t) * (s.reqs.size() + 1),
                         cudaMemcpyDeviceToHost, s.stream);
+        // the status word comes back with the offsets: no round trip when the build is done
+        if (frnn::enqueue_status_read(s.plan, s.stream, s.h_status) != 0) s.build_status = FRNN_ERR_CUDA;
     }
     cudaEventRecord(s.ev_build, s.stream);
     srv->groups[(size_t)s.group].inflight_points += pts;
@@ -264,7 +268,11 @@ void on_built(frnn_server* srv, Slot& s)
     const int nb = (int)s.reqs.size();
     int st = s.build_status;
     unsigned bits = 0;
-    if (st == FRNN_OK) st = frnn::read_status_bits(s.plan, s.stream, &bits);
+    if (st == FRNN_OK) {
+        bits = *static_cast<volatile unsigned*>(s.h_status);  // landed: ev_build follows its copy
+        if ((bits & frnn::kStTimeout) && frnn::recover_after_timeout(s.plan, s.stream) != FRNN_OK)
+            st = FRNN_ERR_CUDA;
+    }
     s.n_ok = 0;
     s.retry_solo = false;
     if (st == FRNN_OK) {
@@ -433,7 +441,8 @@ int create_slot(frnn_server* srv, Slot& s, const frnn_plan_params& pp)
     if (cudaMalloc(reinterpret_cast<void**>(&s.d_in), sizeof(float) * (size_t)(p.batch_points * p.d)) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&s.h_row_ptr), sizeof(int32_t) * (size_t)(p.batch_points + 1), 0) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&s.h_edge_off), sizeof(int32_t) * (size_t)(s.cap_events + 1), 0) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void**>(&s.h_col), sizeof(int32_t) * (size_t)pp.edge_capacity, 0) != cudaSuccess) {
+        cudaHostAlloc(reinterpret_cast<void**>(&s.h_col), sizeof(int32_t) * (size_t)pp.edge_capacity, 0) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&s.h_status), sizeof(unsigned), 0) != cudaSuccess) {
         cudaGetLastError();
         return FRNN_ERR_OOM;
     }
