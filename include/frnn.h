@@ -90,6 +90,10 @@ typedef struct {
                               rows at a time), so that their k nearest are sorted from
                               those instead of walking their candidates again (rows of
                               up to 12 dims); 0 = none.  Speed only, never the result. */
+    uint64_t mem_budget_bytes; /* device memory the plan may take; 0 = no limit.  A plan
+                              whose device bytes (frnn_plan_bytes) exceed it is refused
+                              by frnn_plan_create with FRNN_ERR_OOM before any device
+                              call or allocation                                         */
 } frnn_plan_params;
 
 /*

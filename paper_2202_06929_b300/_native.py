@@ -51,7 +51,8 @@ class frnn_plan_params(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("d_max", ctypes.c_int), ("n_max", ctypes.c_int64),
                 ("events_max", ctypes.c_int), ("k_max_cap", ctypes.c_int),
                 ("edge_capacity", ctypes.c_int64), ("cells_per_point", ctypes.c_int),
-                ("flags", ctypes.c_uint32), ("hit_capacity", ctypes.c_int64)]
+                ("flags", ctypes.c_uint32), ("hit_capacity", ctypes.c_int64),
+                ("mem_budget_bytes", ctypes.c_uint64)]
 
 
 class frnn_csr(ctypes.Structure):
@@ -246,11 +247,12 @@ class Plan:
     def __init__(self, n_max: int, d_max: int, k_max_cap: int, events_max: int = 1,
                  edge_capacity: int = 0, cells_per_point: int = 0, emit_d2: bool = False,
                  use_graph: bool = False, device: int = 0, autotune: bool = False, hit_capacity: int = 0,
-                 debug: bool = False):
+                 debug: bool = False, mem_budget_bytes: int = 0):
         lib = load()
         prm = frnn_plan_params(device=device, d_max=d_max, n_max=n_max, events_max=events_max,
                                k_max_cap=k_max_cap, edge_capacity=edge_capacity,
                                cells_per_point=cells_per_point, hit_capacity=hit_capacity,
+                               mem_budget_bytes=mem_budget_bytes,
                                flags=((FRNN_EMIT_D2 if emit_d2 else 0) | (FRNN_USE_GRAPH if use_graph else 0)
                                       | (FRNN_AUTOTUNE if autotune else 0) | (FRNN_DEBUG if debug else 0)))
         h = ctypes.c_void_p()

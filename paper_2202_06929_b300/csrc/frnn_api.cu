@@ -600,6 +600,7 @@ int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
     long long cells_max = 0;
     const int nrc = normalize_params(prm, &q, &cells_max);
     if (nrc != FRNN_OK) return nrc;
+    if (q.mem_budget_bytes > 0 && plan_device_bytes(q, cells_max) > q.mem_budget_bytes) return FRNN_ERR_OOM;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || q.device < 0 || q.device >= n_dev) {
         cudaGetLastError();

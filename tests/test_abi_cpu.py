@@ -60,6 +60,20 @@ def test_null_plan_and_bad_params_rejected_on_host():
         assert lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)) == 1, bad
 
 
+def test_plan_over_its_memory_budget_is_refused_before_any_device_call():
+    lib = frnn.load()
+    h = ctypes.c_void_p()
+    prm = _native.frnn_plan_params(device=0, d_max=8, n_max=100_000, events_max=1, k_max_cap=64)
+    need = ctypes.c_uint64(0)
+    assert lib.frnn_plan_bytes(ctypes.byref(prm), ctypes.byref(need)) == frnn.FRNN_OK
+    prm.mem_budget_bytes = need.value - 1
+    assert lib.frnn_plan_create(ctypes.byref(h), ctypes.byref(prm)) == frnn.FRNN_ERR_OOM
+    assert not h.value
+    # the budget does not change the plan's size
+    got = ctypes.c_uint64(0)
+    assert lib.frnn_plan_bytes(ctypes.byref(prm), ctypes.byref(got)) == frnn.FRNN_OK and got.value == need.value
+
+
 def test_plan_create_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

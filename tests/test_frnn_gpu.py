@@ -332,6 +332,30 @@ def test_invalid_arguments():
         plan.close()
 
 
+def test_plan_memory_budget():
+    """mem_budget_bytes: a plan whose device bytes exceed the budget is
+    refused with OOM; one at exactly its own size is created, and the device
+    memory it takes is its stated size plus allocation granularity."""
+    kw = dict(n_max=200_000, d_max=8, k_max_cap=64, events_max=4, emit_d2=True)
+    need = frnn.plan_bytes(**kw)
+    with pytest.raises(frnn.FrnnError) as ei:
+        frnn.Plan(mem_budget_bytes=need - 1, **kw)
+    assert ei.value.status == frnn.FRNN_ERR_OOM
+    frnn.Plan(n_max=10, d_max=8, k_max_cap=8).close()  # module and context set-up outside the window
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with frnn.Plan(mem_budget_bytes=need, **kw) as plan:
+        torch.cuda.synchronize()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        assert need <= used <= need + 48 * (2 << 20), (need, used)
+        x = synth.uniform_grid(3000, 8, 5)
+        host = plan.build(torch.from_numpy(x).cuda(), 0.3, 64).to_host()
+        assert plan.last_status() == frnn.FRNN_OK
+    rp, col = oracle.radius_graph(x, 0.3, 64)
+    np.testing.assert_array_equal(host["row_ptr"], rp)
+    np.testing.assert_array_equal(host["col"], col)
+
+
 # ------------------------------------------------------------------ batched form
 
 def _events(kind, sizes, d, seed):
