@@ -594,6 +594,7 @@ int frnn_plan_bytes(const frnn_plan_params* prm, uint64_t* bytes)
 
 int frnn_plan_create(frnn_plan** out, const frnn_plan_params* prm)
 {
+    frnn::NvtxRange nvtx("frnn_plan_create");
     if (!out || !prm) return FRNN_ERR_INVALID_ARG;
     *out = nullptr;
     frnn_plan_params q;
@@ -728,6 +729,7 @@ int frnn_plan_get_tuning(const frnn_plan* p, frnn_tuning* t)
 int frnn_build_graph(frnn_plan* p, const float* emb, int64_t n, int d, float r, int k_max,
                      void* stream, frnn_csr* out)
 {
+    frnn::NvtxRange nvtx("frnn_build_graph");
     if (!p) return FRNN_ERR_INVALID_ARG;
     if (n < 0) return FRNN_ERR_INVALID_ARG;
     const int64_t off[2] = {0, n};
@@ -739,6 +741,7 @@ int frnn_build_graph(frnn_plan* p, const float* emb, int64_t n, int d, float r, 
 int frnn_build_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events,
                              int d, float r, int k_max, void* stream, frnn_csr* out)
 {
+    frnn::NvtxRange nvtx("frnn_build_graph_batched");
     if (!p) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
@@ -748,6 +751,7 @@ int frnn_build_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_o
 int frnn_knn_graph_batched(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, int k,
                            void* stream, frnn_csr* out)
 {
+    frnn::NvtxRange nvtx("frnn_knn_graph_batched");
     if (!p) return FRNN_ERR_INVALID_ARG;
     if (k < 1) return FRNN_ERR_INVALID_ARG;
     long long n_total = 0;
@@ -845,6 +849,7 @@ int frnn_build_graph_profiled(frnn_plan* p, const float* emb, const int64_t* ev_
                               int d, float r, int k_max, void* stream, frnn_csr* out, float* stage_ms,
                               int n_stages)
 {
+    frnn::NvtxRange nvtx("frnn_build_graph_profiled");
     if (!p || !stage_ms || n_stages < kStages) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
@@ -868,6 +873,7 @@ int frnn_build_graph_profiled(frnn_plan* p, const float* emb, const int64_t* ev_
 int frnn_plan_autotune(frnn_plan* p, const float* emb, const int64_t* ev_off, int n_events, int d, float r,
                        int k_max, void* stream, frnn_tuning* best, float* best_ms)
 {
+    frnn::NvtxRange nvtx("frnn_plan_autotune");
     if (!p) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
@@ -886,6 +892,7 @@ int frnn_plan_tuning_for(const frnn_plan* p, const int64_t* ev_off, int n_events
 
 int frnn_label_components(frnn_plan* p, float d2_max, void* stream, int32_t* labels)
 {
+    frnn::NvtxRange nvtx("frnn_label_components");
     if (!p || !labels || std::isnan(d2_max)) return FRNN_ERR_INVALID_ARG;
     if (!p->has_last) return FRNN_ERR_INVALID_ARG;
     const bool all = d2_max >= p->last_r2;
@@ -900,6 +907,7 @@ int frnn_label_components(frnn_plan* p, float d2_max, void* stream, int32_t* lab
 
 int frnn_edge_features(frnn_plan* p, const float* emb, int64_t e_begin, int64_t e_end, float* out, void* stream)
 {
+    frnn::NvtxRange nvtx("frnn_edge_features");
     if (!p || !p->has_last || e_begin < 0 || e_end < e_begin) return FRNN_ERR_INVALID_ARG;
     if (e_end > e_begin && (!emb || !out)) return FRNN_ERR_INVALID_ARG;
     if (e_end > p->edge_cap) return FRNN_ERR_INVALID_ARG;
@@ -919,6 +927,7 @@ int frnn_plan_test_stall_next_build(frnn_plan* p)
 
 int frnn_get_last_status(frnn_plan* p, void* stream)
 {
+    frnn::NvtxRange nvtx("frnn_get_last_status");
     unsigned word = 0;
     const int rc = read_status_bits(p, stream, &word);
     if (rc != FRNN_OK) return rc;
@@ -931,6 +940,7 @@ int frnn_get_last_status(frnn_plan* p, void* stream)
 
 int frnn_check_last_build(frnn_plan* p, void* stream)
 {
+    frnn::NvtxRange nvtx("frnn_check_last_build");
     if (!p || !p->has_last) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;
@@ -964,6 +974,7 @@ int frnn_build_graph_host(frnn_plan* p, const float* h_emb, const int64_t* ev_of
                           int d, float r, int k_max, int32_t* h_row_ptr, int32_t* h_col,
                           int64_t col_capacity, int32_t* h_edge_off, int64_t* h_n_edges, void* stream)
 {
+    frnn::NvtxRange nvtx("frnn_build_graph_host");
     if (!p || !ev_off || !h_row_ptr || !h_n_edges || col_capacity < 0 || n_events < 1) return FRNN_ERR_INVALID_ARG;
     DeviceGuard dg(p->prm.device);
     if (!dg.ok) return FRNN_ERR_CUDA;

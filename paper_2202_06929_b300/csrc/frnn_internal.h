@@ -3,6 +3,8 @@
 
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 struct frnn_plan;
 
 namespace frnn {
@@ -156,6 +158,16 @@ __device__ __forceinline__ bool timed_out(const DevState& st)
     return (__ldcg(st.status) & kStTimeout) != 0u;
 }
 #endif
+
+// A named NVTX range over a host call of the library: the kernels it launches
+// fall inside it for timeline tools and for ncu's --nvtx filters.  Without an
+// attached tool a push or pop costs one test of a function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Forms of the collect walk (frnn_tuning.walk).
 constexpr int kWalkAuto = 0;

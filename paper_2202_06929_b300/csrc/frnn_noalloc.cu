@@ -119,6 +119,7 @@ extern "C" int frnn_build_graph_noalloc(const float* emb, int64_t n, int d, floa
                                         int32_t* row_ptr, int32_t* col, int64_t col_capacity,
                                         int32_t* status, void* stream)
 {
+    frnn::NvtxRange nvtx("frnn_build_graph_noalloc");
     if (n < 0 || d < 1 || k_max < 1 || !row_ptr || !status || col_capacity < 0) return FRNN_ERR_INVALID_ARG;
     if (!(r > 0.0f) || !std::isfinite(r) || !(r * r > 0.0f) || !std::isfinite(r * r)) return FRNN_ERR_INVALID_ARG;
     if (n > 0 && (!emb || (reinterpret_cast<uintptr_t>(emb) & 3u))) return FRNN_ERR_INVALID_ARG;

@@ -228,6 +228,7 @@ std::vector<Slot*> assign_batches(frnn_server* srv)
 // (dispatcher thread, no lock held).
 void launch_batch(frnn_server* srv, Slot& s)
 {
+    frnn::NvtxRange nvtx("frnn_server: launch a batch");
     DeviceGuard dg(s.device);
     const int d = srv->prm.d;
     s.ev_off.assign(1, 0);
@@ -264,6 +265,7 @@ void launch_batch(frnn_server* srv, Slot& s)
 // latched it is rerun one request at a time.
 void on_built(frnn_server* srv, Slot& s)
 {
+    frnn::NvtxRange nvtx("frnn_server: batch built");
     DeviceGuard dg(s.device);
     const int nb = (int)s.reqs.size();
     int st = s.build_status;
@@ -302,6 +304,7 @@ void on_built(frnn_server* srv, Slot& s)
 // ones that did not fit (dispatcher thread; takes mu only to publish).
 void on_copied(frnn_server* srv, Slot& s)
 {
+    frnn::NvtxRange nvtx("frnn_server: batch copied");
     const int nb = (int)s.reqs.size();
     std::vector<Request*> requeue;
     const Clock::time_point now = Clock::now();
@@ -476,6 +479,7 @@ extern "C" {
 
 int frnn_server_create(frnn_server** out, const frnn_server_params* p)
 {
+    frnn::NvtxRange nvtx("frnn_server_create");
     if (!out || !p) return FRNN_ERR_INVALID_ARG;
     *out = nullptr;
     std::vector<int> devices;
@@ -621,6 +625,7 @@ int frnn_server_wait(frnn_server* srv, uint64_t ticket, int32_t* row_ptr, int32_
 int frnn_server_run_trace(frnn_server* srv, const float* host_emb, const int64_t* ev_start, const int64_t* ev_len,
                           const double* arrival_s, int n_events, double* latency_s, int64_t* n_edges, double* wall_s)
 {
+    frnn::NvtxRange nvtx("frnn_server_run_trace");
     if (!srv || !ev_start || !ev_len || !arrival_s || n_events < 0 || !latency_s) return FRNN_ERR_INVALID_ARG;
     const int d = srv->prm.d;
     for (int i = 0; i < n_events; ++i) {
