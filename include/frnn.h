@@ -327,8 +327,9 @@ FRNN_API int frnn_get_last_status(frnn_plan* plan, void* stream);
 /*
  * Debug checks of the plan's last build (radius or kNN), enqueued on `stream`
  * as kernels that only read the build's buffers and the caller's input, which
- * must be unchanged since the build; run them before frnn_label_components,
- * which reuses scratch the checks read.  Each check tests one stage's output
+ * must be unchanged since the build.  Labeling and edge features write nothing
+ * they read, so the checks may run at any point before the plan's next build.
+ * Each check tests one stage's output
  * against what that stage must produce (Sec. 3.4: cell lists, then per-point
  * neighbour lists), in pipeline order:
  *   FRNN_CHECK_EVENT_OFFSETS  edge_off[b] = row_ptr[first point of b], and
