@@ -105,6 +105,19 @@ def test_debug_plan_with_graph_replay_checks_every_build():
         _assert_oracle(csr, xs, 0.1, 32)
 
 
+def test_checks_after_labeling_and_edge_features():
+    """Labeling and edge features write nothing the checks read: checks run
+    after them find a correct build clean."""
+    xs = _events([2500, 1700], 8, 7350)
+    with frnn.Plan(n_max=4200, d_max=8, k_max_cap=32, events_max=2, emit_d2=True) as plan:
+        csr, xt = _build(plan, xs, 0.1, 32)
+        plan.label_components()
+        plan.edge_features(xt, 0, min(1000, csr.n_edges()))
+        assert plan.last_status() == frnn.FRNN_OK
+        plan.check_last_build()
+        _clean(plan)
+
+
 def test_nonfinite_event_and_overflow_are_statuses_not_check_failures():
     xs = _events([1500, 1200, 900], 8, 7400)
     xs[1] = xs[1].copy()
