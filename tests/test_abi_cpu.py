@@ -100,6 +100,18 @@ def test_header_compiles_as_c99_and_links(tmp_path):
     src.write_text('#include "frnn.h"\n'
                    "int main(void) {\n"
                    "    frnn_plan* p = 0;\n"
+                   "    frnn_plan_params prm = {0};\n"
+                   "    uint64_t bytes = 0;\n"
+                   "    int check = -1;\n"
+                   "    int64_t index = 0;\n"
+                   "    prm.d_max = 8; prm.n_max = 1000; prm.events_max = 1; prm.k_max_cap = 16;\n"
+                   "    prm.flags = FRNN_DEBUG | FRNN_EMIT_D2;\n"
+                   "    if (frnn_plan_bytes(&prm, &bytes) != FRNN_OK || bytes == 0) return 2;\n"
+                   "    prm.mem_budget_bytes = bytes - 1;\n"
+                   "    if (frnn_plan_create(&p, &prm) != FRNN_ERR_OOM || p) return 3;\n"
+                   "    if (frnn_check_last_build(p, 0) != FRNN_ERR_INVALID_ARG) return 4;\n"
+                   "    if (frnn_get_last_check(p, 0, &check, &index) != FRNN_ERR_INVALID_ARG) return 5;\n"
+                   "    if (FRNN_CHECK_COMPLETE != 9 || FRNN_ERR_CHECK != 8) return 6;\n"
                    "    return frnn_plan_test_stall_next_build(p) == FRNN_ERR_INVALID_ARG ? 0 : 1;\n"
                    "}\n")
     exe = tmp_path / "use_frnn"
